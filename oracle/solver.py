@@ -24,6 +24,9 @@ Readings of points the paper leaves open (each also listed in the design notes):
   because eps and Ye differ by many orders of magnitude;
 * the constrained least-squares problem is solved by eliminating the
   constraint (alpha_M = 1 - sum of the others) and calling numpy's lstsq;
+* an outer iterate outside the EoS domain (Ye not in (0, 1), or eps outside
+  the range of the EoS at that Ye) sets EOS_FAIL and stops the outer loop; the
+  returned temperature is then the last one inside the domain;
 * after outer convergence the returned matter state is q(M, y) evaluated at
   the converged moments, so lepton number and energy are conserved to
   rounding (final_q=True); final_q=False returns the Anderson-mixed iterate
@@ -48,7 +51,7 @@ ALL_PROCESSES = EMAB | ISO | NES | PAIR
 
 class Params:
     def __init__(self, tol_inner=1e-10, tol_outer=1e-10, M_inner=3, M_outer=3,
-                 max_inner=100, max_outer=100, dmin=1e-30, dmax=1.0 - 1e-6,
+                 max_inner=500, max_outer=100, dmin=1e-30, dmax=1.0 - 1e-6,
                  norm_floor=1e-30, proc_mask=ALL_PROCESSES, frozen_matter=False,
                  final_q=True):
         self.tol_inner = tol_inner
@@ -180,9 +183,6 @@ def solve_node(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, s
     while not outer_converged:
         k += 1
         if k > 1:
-            T, ok = eos.temperature(rho, y[0], y[1])
-            if not ok:
-                status |= EOS_FAIL
             op = compute_opacities(grid, tables, rho, T, y[1], scale, p.proc_mask, p.dmin, p.dmax)
             if op["clamped"]:
                 status |= TABLE_CLAMP
@@ -225,6 +225,13 @@ def solve_node(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, s
         if not outer_converged and k >= p.max_outer:
             status |= NOT_CONVERGED_OUTER
             break
+        if not outer_converged:
+            # reading: an outer iterate outside the EoS domain stops the node
+            T_new, ok = eos.temperature(rho, y[0], y[1])
+            if not ok:
+                status |= EOS_FAIL
+                break
+            T = T_new
 
     if p.frozen_matter:
         y_out, T_out = y_star.copy(), T_star
@@ -233,6 +240,7 @@ def solve_node(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, s
         T_out, ok = eos.temperature(rho, y_out[0], y_out[1])
         if not ok:
             status |= EOS_FAIL
+            T_out = T          # last temperature inside the EoS domain
     return dict(D=M[:, :, 0].copy(), I=M[:, :, 1:].copy(), eps=float(y_out[0]), Ye=float(y_out[1]),
                 T=float(T_out), n_outer=k, n_inner=n_inner, status=status)
 
