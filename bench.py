@@ -1,0 +1,282 @@
+#!/usr/bin/env python
+"""Benchmark: converged collision solves per second on one GB300.
+
+Workload (one step = one collision_solve over every node, inputs resident in
+HBM): collapse-profile states, 2^16 nodes, 4 species (nu_e, anti-nu_e, nu_x,
+anti-nu_x), Grid C with linear elements (16 x 2 = 32 energies), emission/
+absorption + isoenergetic + NES + pair, FP64, Anderson depth 3, tol 1e-10.
+Inputs (J, H of 268 MB) are larger than L2, so every step reads them from HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nmc|reference]
+
+Prints one JSON line.  --impl reference times the CPU oracle (the plain FP64
+restatement of the algorithm) on a bounded sample of the same workload.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_NODES = 1 << 16
+N_ELEM, DE1, NQ, NS = 16, 1.875, 2, 4
+TOL, MEM = 1e-10, 3
+WORKLOAD = ("collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, EmAb+Iso+NES+pair, "
+            "FP64, Anderson depth 3, tol 1e-10")
+FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64: 152 SMs x 4 flop/clk x 2.07 GHz (recipe unit count and clock)
+CPU_SAMPLE = 48           # oracle sample (nodes) for the CPU baseline
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nmc", choices=["nmc", "reference"])
+    ap.add_argument("--nodes", type=int, default=N_NODES)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(seed, nodes, oracle_grid=False):
+    from paper_2601_00976_gb300 import synthetic
+    if oracle_grid:      # the reference arm builds its grid with the oracle's own code
+        from oracle import grid as ogrid
+        edges, _ = ogrid.geometric_edges(N_ELEM, DE1)
+        eps = ogrid.EnergyGrid(edges, NQ).eps
+    else:
+        from paper_2601_00976_gb300 import nmc
+        edges, _ = nmc.geometric_edges(N_ELEM, DE1)
+        eps, _, _ = nmc.grid_nodes(edges, NQ)
+    tables = synthetic.make_tables(eps, NS, seed=0)
+    inp = synthetic.make_inputs("profile", nodes, eps, NS, seed=seed)
+    return edges, eps, tables, inp
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """Time the CPU oracle on a bounded sample of the workload (the reference arm)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import grid as ogrid, solver as osolver
+    edges, _, tables, inp = _workload(0, CPU_SAMPLE, oracle_grid=True)
+    g = ogrid.EnergyGrid(edges, NQ)
+    prm = osolver.Params(tol_inner=TOL, tol_outer=TOL, M_inner=MEM, M_outer=MEM)
+    per = max(4, CPU_SAMPLE // 4)
+    for w in range(args.warmup):
+        osolver.solve(g, tables, prm, inp, nodes=range(w * 2, w * 2 + 2))
+    times = []
+    t_all = time.perf_counter()
+    for k in range(args.steps):
+        nodes = range((k * per) % CPU_SAMPLE, (k * per) % CPU_SAMPLE + per)
+        t0 = time.perf_counter()
+        osolver.solve(g, tables, prm, inp, nodes=nodes)
+        times.append(time.perf_counter() - t0)
+    total = time.perf_counter() - t_all
+    value = per * args.steps / total
+    print(json.dumps({
+        "impl": "reference", "metric": "converged collision solves/s", "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_nodes_per_step": per},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per} nodes of the workload per step, numpy FP64 oracle, one thread"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(edges, tables, inp):
+    from oracle import grid as ogrid, solver as osolver
+    g = ogrid.EnergyGrid(edges, NQ)
+    prm = osolver.Params(tol_inner=TOL, tol_outer=TOL, M_inner=MEM, M_outer=MEM)
+    t0 = time.perf_counter()
+    osolver.solve(g, tables, prm, inp, nodes=range(CPU_SAMPLE))
+    dt = time.perf_counter() - t0
+    return {"value": CPU_SAMPLE / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {CPU_SAMPLE} nodes of the workload, numpy FP64 oracle, one thread, {dt:.1f} s"}
+
+
+def run_nmc(args):
+    import torch
+    from paper_2601_00976_gb300 import nmc, flops
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    edges, eps, tables, inp = _workload(rank, args.nodes)
+    ctx = nmc.Context(edges, NQ, NS, tables)
+    t = {k: torch.tensor(v, device=dev) for k, v in inp.items()}
+    prm = nmc.default_params(tol_inner=TOL, tol_outer=TOL, m_inner=MEM, m_outer=MEM)
+    out = ctx.collision_solve(prm, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.collision_solve(prm, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"], out=out)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    barrier()
+    clk.stop()
+    per_step = [a.elapsed_time(b) for a, b in evs]
+    total_ms = evs[0][0].elapsed_time(evs[-1][1])
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = tt.item()
+    n_in = out["n_inner"].cpu().numpy().astype(np.int64)
+    n_out = out["n_outer"].cpu().numpy().astype(np.int64)
+    status = out["status"].cpu().numpy()
+    fl = float(np.sum(flops.node_flops(NS, len(eps), N_ELEM, NQ, MEM, n_in, n_out)))
+    kern_ms = statistics.mean(per_step)
+    achieved = fl / (kern_ms * 1e-3) / 1e12
+
+    # end to end through the public API with pinned host buffers
+    host = {k: torch.tensor(v).pin_memory() for k, v in inp.items()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    barrier()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.collision_solve(prm, host["rho"], host["T"], host["Ye"], host["D"], host["I"], host["dt"], host["scale"])
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(edges, tables, inp)
+    converged = int(np.count_nonzero(status == 0))
+    if ws > 1:
+        cc = torch.tensor([converged], device=dev, dtype=torch.int64)
+        torch.distributed.all_reduce(cc)
+        converged = int(cc.item())
+    if rank == 0:
+        # converged solves only: a node that stopped at an iteration cap is not counted
+        value = converged * args.steps / (total_ms * 1e-3)
+        clocks = clk.summary()
+        line = {
+            "metric": "converged collision solves/s (nodes*steps/s), FP64", "value": value, "unit": "solves/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes_per_gpu": args.nodes, "l2": "inputs_larger_than_l2",
+                       "mean_inner_iters": float(n_in.mean()), "mean_outer_iters": float(n_out.mean()),
+                       "max_inner_iters": int(n_in.max()), "nodes_flagged": int(np.count_nonzero(status)),
+                       "converged_fraction": converged / (ws * args.nodes)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "fused_fp64_kernel", "peak_source": "derived FP64 FMA rate at 2.07 GHz",
+                         "algorithmic_flops_per_launch": fl, "kernel_ms": kern_ms},
+            "e2e": {"value": ws * converged / (ws * args.nodes) * args.nodes / e2e_s, "unit": "solves/s",
+                    "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_nmc(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * nmc.h -- C ABI of libnmc, a GB300 (sm_103a) implementation of the implicit,
+ * pointwise neutrino--matter collision solve of the thornado DG-IMEX
+ * two-moment scheme (arXiv:2601.00976, Sec. 3.5 "Neutrino--matter coupling").
+ *
+ * At every spatial node the solve finds the primitive moments M = (D, I^j) of
+ * each neutrino species and the matter state y = (eps, Ye) that satisfy the
+ * backward-Euler collision step (Eq. imexImplicit) written as the nested
+ * fixed-point problem M = Q(M, y) (Eq. implicitMomentsNodal) and
+ * y = q(M, y) (Eq. implicitFluidNodal), using Algorithm 1 with Anderson
+ * acceleration and the convergence checks of Algorithms 2 and 3.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Units: energies and temperatures in MeV, rho in g cm^-3, dt in s,
+ *   specific internal energy eps in erg g^-1, opacities in cm^-1.
+ * - The fluid velocity is zero and frozen (as in the paper's deleptonization
+ *   setup), so lambda = 1/(1+|v|) = 1 and only eps and Ye are evolved.
+ * - Species are ordered in particle/antiparticle pairs: (nu_e, anti-nu_e),
+ *   then (nu_x, anti-nu_x) for each heavy flavour; n_species is even.
+ *   Lepton numbers are +1, -1, 0, 0, ... (Sec. 2.2).
+ * - Energy index q = e * n_q + q_eps (element e, LG node q_eps), ne = n_elem * n_q.
+ * - "J" and "H" carry the occupation-normalised moments D and I (Eq.
+ *   primitiveMoments); the energy moments are eps * (D, I) (Sec. 2.2).
+ * - Array arguments of collision_solve / opacity_interp / collision_adjoint are
+ *   DEVICE pointers owned by the caller, contiguous, node-major.  Host arrays
+ *   passed to nmc_create / nmc_energy_nodes / nmc_geometric_edges are HOST
+ *   pointers, read (or written) before the call returns.
+ * - The `stream` argument is a cudaStream_t (NULL = legacy default stream);
+ *   solve and interpolation calls are asynchronous on it.
+ * - Every call returns an int status (NMC_OK or an error code below) and
+ *   never aborts; nmc_last_error() gives a message for the last failure on a
+ *   context.  Numerical trouble at a node is never an error return: it is
+ *   reported in that node's status bits.
+ * - One context may be used by one stream at a time: calls that overlap in
+ *   time on different streams share the context's work-queue counter and race.
+ */
+#ifndef NMC_H
+#define NMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define NMC_OK            0
+#define NMC_EINVAL        1   /* invalid argument (null pointer, bad size, bad parameter) */
+#define NMC_ECUDA         2   /* a CUDA runtime call failed; see nmc_last_error */
+#define NMC_ENOMEM        3   /* device or host allocation failed */
+#define NMC_EUNSUPPORTED  4   /* shape outside what the kernels support (see nmc_create) */
+
+/* ---- per-node status bits (collision_solve) ---- */
+#define NMC_NOT_CONVERGED_INNER 1u   /* some inner loop stopped at max_inner */
+#define NMC_NOT_CONVERGED_OUTER 2u   /* outer loop stopped at max_outer */
+#define NMC_NONFINITE           4u   /* a non-finite moment or matter value appeared */
+#define NMC_EOS_FAIL            8u   /* eps outside the EoS range at some outer iterate; T clamped */
+#define NMC_TABLE_CLAMP        16u   /* a table lookup fell outside the table and was clamped */
+#define NMC_BAD_INPUT          32u   /* rho, T, Ye or dt invalid at this node; outputs = inputs */
+
+/* ---- process mask (Eq. collisionTerm_AllProcesses) ---- */
+#define NMC_PROC_EMAB 1   /* emission/absorption */
+#define NMC_PROC_ISO  2   /* isoenergetic scattering */
+#define NMC_PROC_NES  4   /* neutrino-electron scattering */
+#define NMC_PROC_PAIR 8   /* pair processes */
+#define NMC_PROC_ALL 15
+
+/* ---- precision ---- */
+#define NMC_FP64  0   /* every step in FP64 */
+#define NMC_MIXED 1   /* interpolation, kernel contractions and sweeps in FP32;
+                         conservation sums, matter update, EoS and the Anderson
+                         least-squares solves in FP64 */
+
+/* ---- execution mode ---- */
+#define NMC_MODE_FUSED 0   /* one persistent kernel: each block takes nodes from a
+                              device work queue and runs Algorithm 1 on chip */
+#define NMC_MODE_PLAIN 1   /* one launch per phase and iteration over the still
+                              unconverged nodes */
+
+typedef struct nmc_ctx nmc_ctx;
+
+/* Energy grid of one spatial node (Sec. 3.2, Eq. energy_integration_weights). */
+typedef struct {
+    int32_t n_elem;        /* energy elements, >= 1 */
+    int32_t n_q;           /* LG nodes per element, N = k + 1, 1..3 */
+    int32_t n_species;     /* even, 2..6 */
+    const double* edges;   /* HOST, n_elem + 1 increasing interfaces, edges[0] >= 0 (MeV) */
+} nmc_grid;
+
+/*
+ * Opacity and kernel tables (Sec. 2.3, paragraph on weaklib tables).
+ * All arrays are HOST, C order, float64; nmc_create copies them to the device.
+ *
+ *   emab, iso : [n_species][n_ye][n_t][n_rho][ne]  natural log of chi_EmAb and
+ *               sigma_Iso (cm^-1) on uniform axes in log10 rho, log10 T, Ye;
+ *               the energy axis is the grid's node energies eps_q.
+ *   nes       : [n_species][n_kt][n_eta][ne][ne]   NES Phi_Out(eps_q, eps_q') in
+ *               cm^2 on uniform axes in log10 T and eta_e = mu_e / T; only
+ *               entries with q >= q' are read (down-scattering), the rest
+ *               follows from Eqs. inOutInvarianceNES and detailedBalanceNES.
+ *   pair      : [n_species/2][n_kt][n_eta][ne][ne] pair Phi_Ann(eps_q, eps_q')
+ *               of the particle of each pair, cm^2; the antiparticle's is the
+ *               transpose (Eq. inOutInvariancePair), Phi_Pro follows from
+ *               Eq. detailedBalancePair.
+ * Axis i of n points spans [min, max] uniformly; n >= 2 on every axis.
+ */
+typedef struct {
+    int32_t n_rho, n_t, n_ye;
+    double lrho_min, lrho_max;   /* log10 rho */
+    double lt_min, lt_max;       /* log10 T */
+    double ye_min, ye_max;
+    const double* emab;
+    const double* iso;
+    int32_t n_kt, n_eta;
+    double klt_min, klt_max;     /* log10 T */
+    double eta_min, eta_max;     /* eta_e */
+    const double* nes;
+    const double* pair;
+} nmc_tables;
+
+/* Solver parameters (Algorithm 1 parameters plus the readings the paper leaves open). */
+typedef struct {
+    double  tol_inner;     /* Algorithm 2 relative tolerance */
+    double  tol_outer;     /* Algorithm 3 relative tolerance */
+    int32_t m_inner;       /* Anderson memory M_inner, 1 (Picard) .. 5 */
+    int32_t m_outer;       /* Anderson memory M_outer, 1 .. 5 */
+    int32_t max_inner;     /* cap per inner loop, >= 1 */
+    int32_t max_outer;     /* cap on outer iterations, >= 1 */
+    int32_t precision;     /* NMC_FP64 or NMC_MIXED */
+    int32_t mode;          /* NMC_MODE_FUSED or NMC_MODE_PLAIN */
+    int32_t proc_mask;     /* NMC_PROC_* bits */
+    int32_t frozen_matter; /* 1: y fixed at y*, single outer iteration */
+    int32_t final_q;       /* 1: return y = q(M, y) at the converged moments (exact
+                              conservation); 0: the Anderson-mixed iterate of Alg. 1 */
+    int32_t reserved;
+    double  d_min, d_max;  /* bounds of the D^Eq limiter (Eq. fermiDiracProjection) */
+    double  norm_floor;    /* Algorithm 2 reference norm floored at norm_floor*sqrt(sum W2) */
+} nmc_params;
+
+/* Fills defaults: tol 1e-10, M = 3, caps 100, FP64, fused, all processes,
+ * d_min 1e-30, d_max 1 - 1e-6, norm_floor 1e-30, final_q 1. */
+void nmc_default_params(nmc_params* p);
+
+/*
+ * Creates a context: builds the energy grid, LG rule, W2/W3 weights
+ * (Eq. energy_integration_weights) and the per-element projection operators
+ * of Eq. fermiDiracProjection, and uploads the tables.  Supported shapes:
+ * n_q in 1..3, n_species in {2, 4, 6}, 2 <= ne = n_elem * n_q <= 128, and a
+ * per-block shared-memory footprint <= 227 KB (FP64: ne <= 64 with 4 species).
+ * On success *out owns all device memory it allocated; free it with
+ * nmc_destroy.  On failure *out is NULL and the return code says why.
+ */
+int nmc_create(const nmc_grid* grid, const nmc_tables* tables, nmc_ctx** out);
+
+/* Releases every device and host allocation of the context; NULL is a no-op. */
+void nmc_destroy(nmc_ctx* ctx);
+
+/* Message for the last failed call on ctx (static string if ctx is NULL). */
+const char* nmc_last_error(const nmc_ctx* ctx);
+
+/* Writes the node energies eps_q (MeV), W2_q (cm^-3) and W3_q (MeV cm^-3) of
+ * the context's grid into HOST arrays of length ne (any may be NULL). */
+int nmc_energy_nodes(const nmc_ctx* ctx, double* eps, double* w2, double* w3, int32_t* ne);
+
+/* Node energies eps_q (MeV), W2_q (cm^-3) and W3_q (MeV cm^-3) of `grid`
+ * (Eq. energy_integration_weights) without creating a context: callers use
+ * it to build tables on the node energies.  HOST output arrays of length
+ * n_elem * n_q (any may be NULL). */
+int nmc_grid_nodes(const nmc_grid* grid, double* eps, double* w2, double* w3);
+
+/* Geometric grid of Sec. 3.5.1 (Table energyGrids): n_elem elements on
+ * [0, emax] with widths de1 * alpha^e, alpha solved so they sum to emax.
+ * Writes n_elem + 1 interfaces to HOST `edges` and alpha to *alpha (may be NULL). */
+int nmc_geometric_edges(int32_t n_elem, double de1, double emax, double* edges, double* alpha);
+
+/*
+ * SolveNeutrinoMatterCoupling (Algorithm 1) at n independent nodes.
+ *
+ * Inputs (DEVICE, float64):
+ *   rho[n], T_in[n] (MeV), Ye_in[n]          matter state y* (eps* = eps(rho, T_in, Ye_in))
+ *   J_in[n][ns][ne]                          D* (occupation-normalised zeroth moment)
+ *   H_in[n][ns][ne][3]                       I* (occupation-normalised first moment)
+ *   dt[n]                                    step (s); dtau = c dt (Sec. 3.5: dtau = alpha_ii dt)
+ *   opac_scale[n][4] or NULL                 per-node factors on EmAb, Iso, NES, Pair
+ * Outputs (DEVICE):
+ *   J_out, H_out (same shapes), Ye_out[n], eps_out[n] (erg/g), T_out[n] (MeV),
+ *   n_outer[n], n_inner[n] (total inner iterations), status[n] (NMC_* bits).
+ * Inputs and outputs must not overlap.  n = 0 is a no-op; n <= 2^30.
+ */
+int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n,
+                    const double* rho, const double* T_in, const double* Ye_in,
+                    const double* J_in, const double* H_in, const double* dt,
+                    const double* opac_scale,
+                    double* J_out, double* H_out, double* Ye_out, double* eps_out,
+                    double* T_out, int32_t* n_outer, int32_t* n_inner, uint32_t* status,
+                    void* stream);
+
+/*
+ * Tetralinear table interpolation (Sec. 2.3): value of chi_EmAb (which = 0) or
+ * sigma_Iso (which = 1) of `species` at p points (rho, T, Ye, E), linear in
+ * (log10 rho, log10 T, Ye, ln E) on the table's ln values, exponentiated.
+ * Points outside the table are clamped to its edge.  All arrays DEVICE
+ * float64 of length p; out[p] receives cm^-1.
+ */
+int opacity_interp(nmc_ctx* ctx, int32_t which, int32_t species, int64_t p,
+                   const double* rho, const double* T, const double* Ye, const double* E,
+                   double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMC_H */

@@ -1,0 +1,382 @@
+// C-ABI entry points of libnmc: context set-up (energy grid, quadrature,
+// projection operators, table upload), argument checking and dispatch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nmc_internal.h"
+
+namespace nmc {
+
+int set_error(nmc_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+namespace {
+
+// N-point Gauss--Legendre rule on (-1/2, 1/2) with weights summing to one
+// (Sec. 3.2: LG nodes on the unit reference interval).  Newton iteration on
+// the Legendre recurrence from the Chebyshev-like initial guesses.
+void lg_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) { p1 = z; p0 = 1.0; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[n - 1 - i] = 0.5 * z;                       // ascending order
+        w[n - 1 - i] = 0.5 * 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    if (n == 1) { x[0] = 0.0; w[0] = 1.0; }
+}
+
+double lagrange(const std::vector<double>& nodes, int p, double xi) {
+    double v = 1.0;
+    for (size_t r = 0; r < nodes.size(); ++r)
+        if ((int)r != p) v *= (xi - nodes[r]) / (nodes[p] - nodes[r]);
+    return v;
+}
+
+bool invert_small(std::vector<double>& A, int n) {   // Gauss--Jordan, row-major n x n
+    std::vector<double> I(n * n, 0.0);
+    for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) return false;
+        for (int j = 0; j < n; ++j) { std::swap(A[c * n + j], A[piv * n + j]); std::swap(I[c * n + j], I[piv * n + j]); }
+        const double d = A[c * n + c];
+        for (int j = 0; j < n; ++j) { A[c * n + j] /= d; I[c * n + j] /= d; }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = A[r * n + c];
+            for (int j = 0; j < n; ++j) { A[r * n + j] -= f * A[c * n + j]; I[r * n + j] -= f * I[c * n + j]; }
+        }
+    }
+    A = I;
+    return true;
+}
+
+template <typename T>
+int upload(nmc_ctx* ctx, const T* host, size_t count, const T** dev) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) return set_error(ctx, NMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    ctx->allocations.push_back(p);
+    e = cudaMemcpy(p, host, count * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_error(ctx, NMC_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    *dev = static_cast<const T*>(p);
+    return NMC_OK;
+}
+
+Axis make_axis(double lo, double hi, int n) {
+    Axis a;
+    a.lo = lo;
+    a.inv_d = (n - 1) / (hi - lo);
+    a.n = n;
+    return a;
+}
+
+bool axis_ok(double lo, double hi, int n) { return n >= 2 && std::isfinite(lo) && std::isfinite(hi) && hi > lo; }
+
+}  // namespace
+}  // namespace nmc
+
+using namespace nmc;
+
+extern "C" {
+
+void nmc_default_params(nmc_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->tol_inner = 1e-10;
+    p->tol_outer = 1e-10;
+    p->m_inner = 3;
+    p->m_outer = 3;
+    p->max_inner = 500;
+    p->max_outer = 100;
+    p->precision = NMC_FP64;
+    p->mode = NMC_MODE_FUSED;
+    p->proc_mask = NMC_PROC_ALL;
+    p->frozen_matter = 0;
+    p->final_q = 1;
+    p->d_min = 1e-30;
+    p->d_max = 1.0 - 1e-6;
+    p->norm_floor = 1e-30;
+}
+
+const char* nmc_last_error(const nmc_ctx* ctx) {
+    if (!ctx) return "no context";
+    return ctx->last_error.c_str();
+}
+
+int nmc_geometric_edges(int32_t n_elem, double de1, double emax, double* edges, double* alpha) {
+    if (n_elem < 1 || !(de1 > 0.0) || !(emax > 0.0) || !edges || de1 * n_elem > emax) return NMC_EINVAL;
+    auto total = [&](double a) { double s = 0.0, t = 1.0; for (int i = 0; i < n_elem; ++i) { s += t; t *= a; } return de1 * s; };
+    double lo = 1.0, hi = 4.0;
+    if (total(hi) < emax) return NMC_EINVAL;
+    for (int i = 0; i < 200; ++i) {
+        const double mid = 0.5 * (lo + hi);
+        if (total(mid) < emax) lo = mid; else hi = mid;
+    }
+    const double a = 0.5 * (lo + hi);
+    edges[0] = 0.0;
+    double wdt = de1;
+    for (int i = 0; i < n_elem; ++i) { edges[i + 1] = edges[i] + wdt; wdt *= a; }
+    if (alpha) *alpha = a;
+    return NMC_OK;
+}
+
+int nmc_grid_nodes(const nmc_grid* grid, double* eps, double* w2, double* w3) {
+    if (!grid || !grid->edges || grid->n_elem < 1 || grid->n_q < 1 || grid->n_q > kMaxNq) return NMC_EINVAL;
+    for (int i = 0; i < grid->n_elem; ++i)
+        if (!(grid->edges[i + 1] > grid->edges[i])) return NMC_EINVAL;
+    std::vector<double> xi, wq;
+    lg_rule(grid->n_q, xi, wq);
+    const double hc3 = kHC * kHC * kHC;
+    for (int el = 0; el < grid->n_elem; ++el) {
+        const double c = 0.5 * (grid->edges[el] + grid->edges[el + 1]);
+        const double h = grid->edges[el + 1] - grid->edges[el];
+        for (int k = 0; k < grid->n_q; ++k) {
+            const int q = el * grid->n_q + k;
+            const double ep = c + h * xi[k];
+            const double v2 = 4.0 * kPi * wq[k] * ep * ep * h / hc3;
+            if (eps) eps[q] = ep;
+            if (w2) w2[q] = v2;
+            if (w3) w3[q] = v2 * ep;
+        }
+    }
+    return NMC_OK;
+}
+
+int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
+    if (!out) return NMC_EINVAL;
+    *out = nullptr;
+    if (!grid || !tb || !grid->edges) return NMC_EINVAL;
+    const int n_elem = grid->n_elem, nq = grid->n_q, ns = grid->n_species;
+    if (n_elem < 1 || nq < 1 || nq > kMaxNq || ns < 2 || ns > kMaxSpecies || (ns & 1)) return NMC_EINVAL;
+    const int ne = n_elem * nq;
+    if (ne > kMaxNe || ne < 2) return NMC_EUNSUPPORTED;
+    for (int i = 0; i < n_elem; ++i)
+        if (!(grid->edges[i + 1] > grid->edges[i]) || !std::isfinite(grid->edges[i + 1])) return NMC_EINVAL;
+    if (!(grid->edges[0] >= 0.0)) return NMC_EINVAL;
+    if (!tb->emab || !tb->iso || !tb->nes || !tb->pair) return NMC_EINVAL;
+    if (!axis_ok(tb->lrho_min, tb->lrho_max, tb->n_rho) || !axis_ok(tb->lt_min, tb->lt_max, tb->n_t) ||
+        !axis_ok(tb->ye_min, tb->ye_max, tb->n_ye) || !axis_ok(tb->klt_min, tb->klt_max, tb->n_kt) ||
+        !axis_ok(tb->eta_min, tb->eta_max, tb->n_eta))
+        return NMC_EINVAL;
+
+    nmc_ctx* ctx = new (std::nothrow) nmc_ctx();
+    if (!ctx) return NMC_ENOMEM;
+    ctx->n_elem = n_elem;
+    ctx->nq = nq;
+    ctx->ns = ns;
+    ctx->ne = ne;
+    int nep = 1;
+    if (ne <= 32) { while (nep < ne) nep <<= 1; } else { nep = ((ne + 31) / 32) * 32; }
+    ctx->nep = nep;
+    if (ns * nep > 1024) { delete ctx; return NMC_EUNSUPPORTED; }
+
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    if (e != cudaSuccess) { delete ctx; return NMC_ECUDA; }
+
+    // ---- energy grid and weights (Eq. energy_integration_weights) ----
+    std::vector<double> xi, wq, xg, wg;
+    lg_rule(nq, xi, wq);
+    lg_rule(kProjQuad, xg, wg);
+    ctx->edges.assign(grid->edges, grid->edges + n_elem + 1);
+    ctx->eps.resize(ne);
+    ctx->w2.resize(ne);
+    ctx->w3.resize(ne);
+    std::vector<double> lneps(ne);
+    double sum_w2 = 0.0;
+    const double hc3 = kHC * kHC * kHC;
+    for (int el = 0; el < n_elem; ++el) {
+        const double c = 0.5 * (ctx->edges[el] + ctx->edges[el + 1]);
+        const double h = ctx->edges[el + 1] - ctx->edges[el];
+        for (int k = 0; k < nq; ++k) {
+            const int q = el * nq + k;
+            const double ep = c + h * xi[k];
+            ctx->eps[q] = ep;
+            ctx->w2[q] = 4.0 * kPi * wq[k] * ep * ep * h / hc3;
+            ctx->w3[q] = ctx->w2[q] * ep;
+            lneps[q] = std::log(ep);
+            sum_w2 += ctx->w2[q];
+        }
+    }
+    // ---- projection operators of Eq. fermiDiracProjection per element ----
+    const int Q = kProjQuad;
+    std::vector<double> pe(n_elem * Q), pc(n_elem * nq * Q), pa(n_elem * Q);
+    for (int el = 0; el < n_elem; ++el) {
+        const double c = 0.5 * (ctx->edges[el] + ctx->edges[el + 1]);
+        const double h = ctx->edges[el + 1] - ctx->edges[el];
+        std::vector<double> wt(Q), L(nq * Q);
+        double swt = 0.0;
+        for (int gq = 0; gq < Q; ++gq) {
+            const double eg = c + h * xg[gq];
+            pe[el * Q + gq] = eg;
+            wt[gq] = wg[gq] * eg * eg * h;          // eps^2 d eps
+            swt += wt[gq];
+            for (int p = 0; p < nq; ++p) L[p * Q + gq] = lagrange(xi, p, xg[gq]);
+        }
+        std::vector<double> M(nq * nq, 0.0);
+        for (int p = 0; p < nq; ++p)
+            for (int r = 0; r < nq; ++r)
+                for (int gq = 0; gq < Q; ++gq) M[p * nq + r] += wt[gq] * L[p * Q + gq] * L[r * Q + gq];
+        if (!invert_small(M, nq)) { delete ctx; return NMC_EINVAL; }
+        for (int p = 0; p < nq; ++p)
+            for (int gq = 0; gq < Q; ++gq) {
+                double v = 0.0;
+                for (int r = 0; r < nq; ++r) v += M[p * nq + r] * wt[gq] * L[r * Q + gq];
+                pc[(el * nq + p) * Q + gq] = v;
+            }
+        for (int gq = 0; gq < Q; ++gq) pa[el * Q + gq] = wt[gq] / swt;
+    }
+    DevGrid& g = ctx->g;
+    g.ns = ns;
+    g.ne = ne;
+    g.nep = nep;
+    g.n_elem = n_elem;
+    g.nq = nq;
+    g.ld = ne + 1;
+    g.sum_w2 = sum_w2;
+    for (int p = 0; p < kMaxNq; ++p) {
+        g.ends[0][p] = p < nq ? lagrange(xi, p, -0.5) : 0.0;
+        g.ends[1][p] = p < nq ? lagrange(xi, p, 0.5) : 0.0;
+    }
+    int rc = NMC_OK;
+    if (rc == NMC_OK) rc = upload(ctx, ctx->eps.data(), ne, &g.eps);
+    if (rc == NMC_OK) rc = upload(ctx, ctx->w2.data(), ne, &g.w2);
+    if (rc == NMC_OK) rc = upload(ctx, ctx->w3.data(), ne, &g.w3);
+    if (rc == NMC_OK) rc = upload(ctx, lneps.data(), ne, &g.lneps);
+    if (rc == NMC_OK) rc = upload(ctx, pe.data(), pe.size(), &g.proj_e);
+    if (rc == NMC_OK) rc = upload(ctx, pc.data(), pc.size(), &g.proj_c);
+    if (rc == NMC_OK) rc = upload(ctx, pa.data(), pa.size(), &g.proj_a);
+
+    // ---- tables ----
+    DevTables& t = ctx->tb;
+    t.rho = make_axis(tb->lrho_min, tb->lrho_max, tb->n_rho);
+    t.t = make_axis(tb->lt_min, tb->lt_max, tb->n_t);
+    t.ye = make_axis(tb->ye_min, tb->ye_max, tb->n_ye);
+    t.kt = make_axis(tb->klt_min, tb->klt_max, tb->n_kt);
+    t.eta = make_axis(tb->eta_min, tb->eta_max, tb->n_eta);
+    const size_t n_op = (size_t)ns * tb->n_ye * tb->n_t * tb->n_rho * ne;
+    const size_t n_nes = (size_t)ns * tb->n_kt * tb->n_eta * ne * ne;
+    const size_t n_pair = (size_t)(ns / 2) * tb->n_kt * tb->n_eta * ne * ne;
+    if (rc == NMC_OK) rc = upload(ctx, tb->emab, n_op, &t.emab);
+    if (rc == NMC_OK) rc = upload(ctx, tb->iso, n_op, &t.iso);
+    if (rc == NMC_OK) rc = upload(ctx, tb->nes, n_nes, &t.nes);
+    if (rc == NMC_OK) rc = upload(ctx, tb->pair, n_pair, &t.pair);
+    if (rc == NMC_OK) {
+        void* p = nullptr;
+        e = cudaMalloc(&p, 256);
+        if (e != cudaSuccess) rc = NMC_ENOMEM;
+        else { ctx->allocations.push_back(p); ctx->queue = static_cast<int*>(p); }
+    }
+    if (rc != NMC_OK) { nmc_destroy(ctx); return rc; }
+    *out = ctx;
+    return NMC_OK;
+}
+
+void nmc_destroy(nmc_ctx* ctx) {
+    if (!ctx) return;
+    for (void* p : ctx->allocations) cudaFree(p);
+    delete ctx;
+}
+
+int nmc_energy_nodes(const nmc_ctx* ctx, double* eps, double* w2, double* w3, int32_t* ne) {
+    if (!ctx) return NMC_EINVAL;
+    if (ne) *ne = ctx->ne;
+    for (int q = 0; q < ctx->ne; ++q) {
+        if (eps) eps[q] = ctx->eps[q];
+        if (w2) w2[q] = ctx->w2[q];
+        if (w3) w3[q] = ctx->w3[q];
+    }
+    return NMC_OK;
+}
+
+static int check_params(nmc_ctx* ctx, const nmc_params* p) {
+    if (!p) return set_error(ctx, NMC_EINVAL, "params is NULL");
+    if (!(p->tol_inner > 0.0) || !(p->tol_outer > 0.0) || !std::isfinite(p->tol_inner) || !std::isfinite(p->tol_outer))
+        return set_error(ctx, NMC_EINVAL, "tolerances must be positive and finite");
+    if (p->m_inner < 1 || p->m_inner > 5 || p->m_outer < 1 || p->m_outer > kMaxOuterMem)
+        return set_error(ctx, NMC_EINVAL, "Anderson memory must be in 1..5");
+    if (p->max_inner < 1 || p->max_outer < 1) return set_error(ctx, NMC_EINVAL, "iteration caps must be >= 1");
+    if (p->precision != NMC_FP64 && p->precision != NMC_MIXED) return set_error(ctx, NMC_EINVAL, "unknown precision");
+    if (p->mode != NMC_MODE_FUSED && p->mode != NMC_MODE_PLAIN) return set_error(ctx, NMC_EINVAL, "unknown mode");
+    if (p->proc_mask < 0 || p->proc_mask > NMC_PROC_ALL) return set_error(ctx, NMC_EINVAL, "bad process mask");
+    if (!(p->d_min > 0.0) || !(p->d_max < 1.0) || !(p->d_min < p->d_max))
+        return set_error(ctx, NMC_EINVAL, "need 0 < d_min < d_max < 1");
+    if (!(p->norm_floor >= 0.0)) return set_error(ctx, NMC_EINVAL, "norm_floor must be >= 0");
+    return NMC_OK;
+}
+
+int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n, const double* rho,
+                    const double* T_in, const double* Ye_in, const double* J_in, const double* H_in,
+                    const double* dt, const double* opac_scale, double* J_out, double* H_out,
+                    double* Ye_out, double* eps_out, double* T_out, int32_t* n_outer,
+                    int32_t* n_inner, uint32_t* status, void* stream) {
+    if (!ctx) return NMC_EINVAL;
+    int rc = check_params(ctx, params);
+    if (rc != NMC_OK) return rc;
+    if (n < 0) return set_error(ctx, NMC_EINVAL, "n < 0");
+    if (n > (int64_t(1) << 30)) return set_error(ctx, NMC_EUNSUPPORTED, "n > 2^30 nodes per call");
+    if (n == 0) return NMC_OK;
+    if (!rho || !T_in || !Ye_in || !J_in || !H_in || !dt || !J_out || !H_out || !Ye_out || !eps_out ||
+        !T_out || !n_outer || !n_inner || !status)
+        return set_error(ctx, NMC_EINVAL, "null array argument");
+    if (params->precision != NMC_FP64)
+        return set_error(ctx, NMC_EUNSUPPORTED, "mixed precision is not available in this build");
+    if (params->mode != NMC_MODE_FUSED)
+        return set_error(ctx, NMC_EUNSUPPORTED, "plain mode is not available in this build");
+    SolveArgs a{};
+    a.g = ctx->g;
+    a.tb = ctx->tb;
+    a.p = *params;
+    a.n = n;
+    a.rho = rho; a.T = T_in; a.Ye = Ye_in; a.J = J_in; a.H = H_in; a.dt = dt; a.scale = opac_scale;
+    a.J_out = J_out; a.H_out = H_out; a.Ye_out = Ye_out; a.eps_out = eps_out; a.T_out = T_out;
+    a.n_outer = n_outer; a.n_inner = n_inner; a.status = status;
+    a.queue = ctx->queue;
+    return launch_fused_fp64(ctx, a, static_cast<cudaStream_t>(stream));
+}
+
+int opacity_interp(nmc_ctx* ctx, int32_t which, int32_t species, int64_t p, const double* rho,
+                   const double* T, const double* Ye, const double* E, double* out, void* stream) {
+    if (!ctx) return NMC_EINVAL;
+    if (which != 0 && which != 1) return set_error(ctx, NMC_EINVAL, "which must be 0 (EmAb) or 1 (Iso)");
+    if (species < 0 || species >= ctx->ns) return set_error(ctx, NMC_EINVAL, "species out of range");
+    if (p < 0) return set_error(ctx, NMC_EINVAL, "p < 0");
+    if (p == 0) return NMC_OK;
+    if (!rho || !T || !Ye || !E || !out) return set_error(ctx, NMC_EINVAL, "null array argument");
+    return launch_opacity_interp(ctx, which, species, p, rho, T, Ye, E, out, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

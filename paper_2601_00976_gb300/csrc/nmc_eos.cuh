@@ -1,0 +1,76 @@
+// Synthetic closed-form equation of state on the device (FP64).
+//
+// Stands in for the tabulated EoS the paper interpolates with weaklib
+// (Sec. 3.5.2, paragraph after Eq. eulerianNumberLG): a massless e+e- gas
+// (exact Fermi--Dirac moments), a non-degenerate nucleon gas and photons.
+//   n_e   = (mu^3 + pi^2 T^2 mu) / (3 pi^2 (hbar c)^3) = rho Ye / m_B
+//   u_e   = (7 pi^2 T^4/60 + T^2 mu^2/2 + mu^4/(4 pi^2)) / (hbar c)^3
+//   u_N   = 1.5 T rho / m_B,   u_gamma = pi^2 T^4 / (15 (hbar c)^3)
+//   eps   = (u_e + u_N + u_gamma) / rho        [erg/g after unit conversion]
+//   mu_nue = mu_e - T ln((1-Ye)/Ye) - (m_n - m_p),  mu_anue = -mu_nue, mu_x = 0.
+#pragma once
+
+#include "nmc_internal.h"
+
+namespace nmc {
+
+__device__ __forceinline__ double eos_mu_e(double rho, double T, double Ye) {
+    const double pi2 = kPi * kPi;
+    const double hc3 = kHbarC * kHbarC * kHbarC;
+    const double ne = Ye * rho / kMB;
+    const double p = pi2 * T * T;
+    const double q = -3.0 * pi2 * hc3 * ne;
+    // real root of x^3 + p x + q = 0 (p > 0): hyperbolic form of Cardano's solution
+    return -2.0 * sqrt(p / 3.0) * sinh(asinh(1.5 * q / p * sqrt(3.0 / p)) / 3.0);
+}
+
+// eps(rho, T, Ye) in erg/g and d eps / dT at fixed rho, Ye.
+__device__ __forceinline__ void eos_eps(double rho, double T, double Ye, double* eps, double* deps) {
+    const double pi2 = kPi * kPi;
+    const double hc3 = kHbarC * kHbarC * kHbarC;
+    const double mu = eos_mu_e(rho, T, Ye);
+    const double T2 = T * T, mu2 = mu * mu;
+    const double ue = (7.0 * pi2 * T2 * T2 / 60.0 + 0.5 * T2 * mu2 + mu2 * mu2 / (4.0 * pi2)) / hc3;
+    const double nb = rho / kMB;
+    const double ug = pi2 / 15.0 * T2 * T2 / hc3;
+    const double f = kMeVErg / rho;
+    *eps = (ue + 1.5 * T * nb + ug) * f;
+    // mu(T) at fixed n_e: dmu/dT = -(dn/dT)/(dn/dmu) = -2 pi^2 T mu / (3 mu^2 + pi^2 T^2)
+    const double dmu = -2.0 * pi2 * T * mu / (3.0 * mu2 + pi2 * T2);
+    const double due = (7.0 * pi2 * T2 * T / 15.0 + T * mu2 + (T2 * mu + mu2 * mu / pi2) * dmu) / hc3;
+    *deps = (due + 1.5 * nb + 4.0 * pi2 / 15.0 * T2 * T / hc3) * f;
+}
+
+// T with eps(rho, T, Ye) = eps_t: safeguarded Newton in T, bracketed by
+// [kTMin, kTMax].  *ok = false (and T clamped) when eps_t is outside the range.
+__device__ double eos_temperature(double rho, double eps_t, double Ye, double T0, bool* ok) {
+    *ok = true;
+    if (!(Ye > 0.0 && Ye < 1.0) || !isfinite(eps_t)) {
+        *ok = false;
+        return isfinite(T0) ? T0 : 1.0;
+    }
+    double lo = kTMin, hi = kTMax, e, de;
+    eos_eps(rho, lo, Ye, &e, &de);
+    if (eps_t <= e) { *ok = false; return lo; }
+    eos_eps(rho, hi, Ye, &e, &de);
+    if (eps_t >= e) { *ok = false; return hi; }
+    double T = (T0 > lo && T0 < hi) ? T0 : sqrt(lo * hi);
+    for (int it = 0; it < 200; ++it) {
+        eos_eps(rho, T, Ye, &e, &de);
+        const double f = e - eps_t;
+        if (f > 0.0) hi = T; else lo = T;
+        if (f == 0.0) break;
+        double Tn = T - f / de;
+        if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+        const double d = fabs(Tn - T);
+        T = Tn;
+        if (d <= 2e-16 * T || hi - lo <= 4e-16 * hi) break;
+    }
+    return T;
+}
+
+__device__ __forceinline__ double eos_mu_hat(double T, double Ye) {
+    return T * log((1.0 - Ye) / Ye) + kDmNP;
+}
+
+}  // namespace nmc

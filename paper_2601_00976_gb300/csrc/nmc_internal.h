@@ -1,0 +1,110 @@
+// Internal definitions shared by the translation units of libnmc.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "nmc.h"
+
+namespace nmc {
+
+// Gauss--Legendre points per element used for the right-hand side of the
+// D^Eq projection (Eq. fermiDiracProjection); integrand of the mass matrix is a
+// polynomial of degree <= 2k+2 <= 6, so it is integrated exactly as well.
+constexpr int kProjQuad = 16;
+constexpr int kMaxSpecies = 6;
+constexpr int kMaxNq = 3;
+constexpr int kMaxNe = 128;
+constexpr int kMaxOuterMem = 5;
+
+// Physical constants (MeV, cm, g, s).
+constexpr double kC = 2.99792458e10;               // cm/s
+constexpr double kHC = 1.23984198e-10;             // MeV cm
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kHbarC = kHC / (2.0 * kPi);       // MeV cm
+constexpr double kMB = 1.66053906660e-24;          // g (average baryon mass)
+constexpr double kMeVErg = 1.602176634e-6;         // erg/MeV
+constexpr double kDmNP = 1.2933;                   // MeV
+constexpr double kTMin = 1.0e-3;                   // MeV, EoS range
+constexpr double kTMax = 1.0e3;
+
+// Uniform table axis: value v maps to x = (v - lo) * inv_d with cell floor(x).
+struct Axis {
+    double lo, inv_d;
+    int n;
+};
+
+// Everything the kernels need about one context, passed by value.
+struct DevGrid {
+    int ns, ne, nep, n_elem, nq, ld;   // nep: padded energies per species group; ld = ne + 1
+    const double* eps;     // [ne]
+    const double* w2;      // [ne]
+    const double* w3;      // [ne]
+    const double* lneps;   // [ne] ln eps (opacity_interp energy axis)
+    const double* proj_e;  // [n_elem][Q] quadrature energies
+    const double* proj_c;  // [n_elem][nq][Q] projection operator (mass^-1 * basis * weights)
+    const double* proj_a;  // [n_elem][Q] eps^2-weighted cell-average weights
+    double ends[2][kMaxNq];  // ell_p(-1/2), ell_p(+1/2)
+    double sum_w2;
+};
+
+struct DevTables {
+    Axis rho, t, ye, kt, eta;
+    const double* emab;    // [ns][nye][nt][nrho][ne] ln chi
+    const double* iso;
+    const double* nes;     // [ns][nkt][neta][ne][ne]
+    const double* pair;    // [ns/2][nkt][neta][ne][ne]
+};
+
+struct SolveArgs {
+    DevGrid g;
+    DevTables tb;
+    nmc_params p;
+    long long n;
+    const double* rho;
+    const double* T;
+    const double* Ye;
+    const double* J;
+    const double* H;
+    const double* dt;
+    const double* scale;
+    double* J_out;
+    double* H_out;
+    double* Ye_out;
+    double* eps_out;
+    double* T_out;
+    int32_t* n_outer;
+    int32_t* n_inner;
+    uint32_t* status;
+    int* queue;
+    // shared-memory carve (offsets in doubles)
+    int off_phi, off_ann, off_vec, off_red, off_node;
+};
+
+}  // namespace nmc
+
+struct nmc_ctx {
+    int n_elem = 0, nq = 0, ns = 0, ne = 0, nep = 0;
+    std::vector<double> edges, eps, w2, w3;
+    nmc::DevGrid g{};
+    nmc::DevTables tb{};
+    // device allocations owned by the context
+    std::vector<void*> allocations;
+    int* queue = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    std::string last_error;
+};
+
+namespace nmc {
+// launchers (nmc_solve.cu, nmc_interp.cu)
+int launch_fused_fp64(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream);
+int launch_opacity_interp(nmc_ctx* ctx, int which, int species, long long p, const double* rho,
+                          const double* T, const double* Ye, const double* E, double* out,
+                          cudaStream_t stream);
+size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, SolveArgs* a);
+int set_error(nmc_ctx* ctx, int code, const std::string& msg);
+}  // namespace nmc

@@ -1,0 +1,77 @@
+// opacity_interp: tetralinear interpolation of the EmAb / Iso log tables at
+// arbitrary points (Sec. 2.3, tetralinear interpolation of chi_EmAb and the
+// isoenergetic kernels).  One thread per point: uniform axes in
+// (log10 rho, log10 T, Ye) give the cell directly, the energy axis (the node
+// energies of the grid) is searched by bisection in ln E; the 16 corner ln
+// values are combined with the tensor-product weights and exponentiated.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "nmc_internal.h"
+
+namespace nmc {
+
+namespace {
+
+__device__ __forceinline__ void cell(double v, const Axis& ax, int* i, double* t) {
+    double x = (v - ax.lo) * ax.inv_d;
+    if (!(x >= 0.0)) x = 0.0;
+    if (x > ax.n - 1) x = ax.n - 1;
+    int c = (int)floor(x);
+    if (c > ax.n - 2) c = ax.n - 2;
+    *i = c;
+    *t = x - c;
+}
+
+__global__ void opacity_interp_kernel(const DevGrid g, const DevTables tb, int which, int species,
+                                      long long p, const double* __restrict__ rho,
+                                      const double* __restrict__ T, const double* __restrict__ Ye,
+                                      const double* __restrict__ E, double* __restrict__ out) {
+    const double* tab = which == 0 ? tb.emab : tb.iso;
+    const int NE = g.ne;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p; i += (long long)gridDim.x * blockDim.x) {
+        int ir, it, iy;
+        double tr, tt, ty;
+        cell(log10(rho[i]), tb.rho, &ir, &tr);
+        cell(log10(T[i]), tb.t, &it, &tt);
+        cell(Ye[i], tb.ye, &iy, &ty);
+        // energy: ln E clamped to [ln eps_0, ln eps_{ne-1}], bisection for the cell
+        double le = log(E[i]);
+        if (!(le >= g.lneps[0])) le = g.lneps[0];
+        if (le > g.lneps[NE - 1]) le = g.lneps[NE - 1];
+        int lo = 0, hi = NE - 1;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (g.lneps[mid] <= le) lo = mid; else hi = mid;
+        }
+        const double te = (le - g.lneps[lo]) / (g.lneps[lo + 1] - g.lneps[lo]);
+        const long long base = ((((long long)species * tb.ye.n + iy) * tb.t.n + it) * tb.rho.n + ir) * NE + lo;
+        const long long dR = NE, dT = (long long)tb.rho.n * NE, dY = (long long)tb.t.n * tb.rho.n * NE;
+        double v = 0.0;
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+            const int ca = c8 & 1, cb = (c8 >> 1) & 1, cc = c8 >> 2;
+            const double w = (ca ? tr : 1.0 - tr) * (cb ? tt : 1.0 - tt) * (cc ? ty : 1.0 - ty);
+            const long long o = base + ca * dR + cb * dT + cc * dY;
+            v += w * ((1.0 - te) * tab[o] + te * tab[o + 1]);
+        }
+        out[i] = exp(v);
+    }
+}
+
+}  // namespace
+
+int launch_opacity_interp(nmc_ctx* ctx, int which, int species, long long p, const double* rho,
+                          const double* T, const double* Ye, const double* E, double* out,
+                          cudaStream_t stream) {
+    const int threads = 256;
+    long long blocks = (p + threads - 1) / threads;
+    const long long cap = (long long)ctx->num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    opacity_interp_kernel<<<(unsigned)blocks, threads, 0, stream>>>(ctx->g, ctx->tb, which, species, p, rho, T, Ye, E, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(ctx, NMC_ECUDA, std::string("opacity_interp launch: ") + cudaGetErrorString(e));
+    return NMC_OK;
+}
+
+}  // namespace nmc

@@ -1,0 +1,43 @@
+"""Algorithmic floating-point work of one collision solve (roofline numerator).
+
+Counts the arithmetic Algorithm 1 requires, not what a kernel happens to
+execute: an FMA is 2 flops; an add, multiply, divide, square root, exp or log is
+1 flop.  Per node, with L = 4 ns ne unknowns and Anderson memory m:
+
+inner iteration
+  rates (Eqs. nesRatesNodal, pairRatesNodal): NES 2 mat-vecs and pair 2 mat-vecs
+  per species, 2 ne^2 flops each                         -> 8 ns ne^2
+  vectors, totals, map Q, residual, Gram row, mixing, Algorithm 2
+                                                         -> (13 + 4 m) L
+outer iteration (ComputeOpacities + matter update)
+  EoS root find (about 6 Newton steps of ~100 flops)     -> 600
+  Fermi-Dirac at 16 points per element (exp + 3)         -> 4 * 16 ns n_elem
+  projection (2 (nq + 1) per point) and limiter          -> 2 (nq+1) 16 ns n_elem + 20 ns n_elem
+  EmAb/Iso trilinear + exp (2 tables, 33 each)           -> 66 ns ne
+  NES lower triangle bilinear (9), upper by detailed balance (2),
+  pair bilinear (9)                                      -> 9 ns ne(ne+1)/2 + 2 ns ne(ne-1)/2 + 9 (ns/2) ne^2
+  D/(1-D), norms, matter sums                            -> 11 ns ne
+final: EoS root find 600, initial sums 4 ns ne.
+"""
+
+
+def inner_flops(ns, ne, m, nes=True, pair=True):
+    L = 4 * ns * ne
+    mv = (4 * ns * ne * ne if nes else 0) + (4 * ns * ne * ne if pair else 0)
+    return mv + (13 + 4 * m) * L
+
+
+def outer_flops(ns, ne, n_elem, nq, nes=True, pair=True):
+    f = 600 + 4 * 16 * ns * n_elem + 2 * (nq + 1) * 16 * ns * n_elem + 20 * ns * n_elem
+    f += 66 * ns * ne + 11 * ns * ne
+    if nes:
+        f += 9 * ns * ne * (ne + 1) // 2 + 2 * ns * ne * (ne - 1) // 2
+    if pair:
+        f += 9 * (ns // 2) * ne * ne
+    return f
+
+
+def node_flops(ns, ne, n_elem, nq, m, n_inner, n_outer, nes=True, pair=True):
+    """Total flops of one node given its inner and outer iteration counts (arrays ok)."""
+    return (n_inner * inner_flops(ns, ne, m, nes, pair) + n_outer * outer_flops(ns, ne, n_elem, nq, nes, pair)
+            + 600 + 4 * ns * ne)
