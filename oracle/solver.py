@@ -24,6 +24,9 @@ Readings of points the paper leaves open (each also listed in the design notes):
   because eps and Ye differ by many orders of magnitude;
 * the constrained least-squares problem is solved by eliminating the
   constraint (alpha_M = 1 - sum of the others) and calling numpy's lstsq;
+* an inner loop that reaches max_inner without converging ends the node
+  before its matter update (NOT_CONVERGED_INNER), so a node that does not
+  converge costs at most one capped inner loop more than one that does;
 * an outer iterate outside the EoS domain (Ye not in (0, 1), or eps outside
   the range of the EoS at that Ye) sets EOS_FAIL and stops the outer loop; the
   returned temperature is then the last one inside the domain;
@@ -210,6 +213,10 @@ def solve_node(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, s
                 break
         if p.frozen_matter:
             break
+        if status & (NOT_CONVERGED_INNER | NONFINITE):
+            # reading: an inner loop stopped at its cap (or a non-finite moment)
+            # ends the node before its matter update
+            break
         qv = matter_map(M[:, :, 0], rho, y_star, EN_star, grid, g)
         f = (qv - y) / np.abs(y_star)
         q_hist.append(qv)
@@ -219,7 +226,7 @@ def solve_node(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, s
         y_new = sum(b * qj for b, qj in zip(beta, q_hist))
         outer_converged = check_outer(y_new - y, y_star, p.tol_outer)
         y = y_new
-        if status & NONFINITE or not np.all(np.isfinite(y)):
+        if not np.all(np.isfinite(y)):
             status |= NONFINITE
             break
         if not outer_converged and k >= p.max_outer:
@@ -235,6 +242,9 @@ def solve_node(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, s
 
     if p.frozen_matter:
         y_out, T_out = y_star.copy(), T_star
+    elif status & NONFINITE:
+        y_out = y                  # last matter iterate; T is its temperature
+        T_out = T
     else:
         y_out = matter_map(M[:, :, 0], rho, y_star, EN_star, grid, g) if p.final_q else y
         T_out, ok = eos.temperature(rho, y_out[0], y_out[1])

@@ -531,7 +531,8 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
                 for (int c = 0; c < 4; ++c) M[c] = Mn[c];
                 if (nd->conv_in) break;
             }
-            if (P.frozen_matter || nd->bad) { outer_exit = 1; }
+            // an inner loop stopped at its cap (or a non-finite moment) ends the node
+            if (P.frozen_matter || nd->bad || (nd->status & NMC_NOT_CONVERGED_INNER)) { outer_exit = 1; }
             // ================= matter update (Eq. implicitFluidNodal) =================
             if (!outer_exit) {
                 double v[2] = {W3q * M[0], gs * W2q * M[0]};
@@ -583,6 +584,14 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
             }
         }
         // ================= finalize =================
+        {   // q(M, y) at the final moments (Eq. implicitFluidNodal)
+            double v[2] = {W3q * M[0], gs * W2q * M[0]};
+            block_sum<2>(v, red, nd->blk_out);
+            if (tid == 0) {
+                nd->qv[0] = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * kMeVErg / nd->rho;
+                nd->qv[1] = nd->ystar[1] - kMB * (nd->blk_out[1] - nd->EN_star[1]) / nd->rho;
+            }
+        }
         if (tid == 0) {
             const double rho = nd->rho;
             double yo0, yo1, To;

@@ -17,7 +17,8 @@ available; smooth seeded stand-ins with the same structure take their place:
   each particle/antiparticle pair, both positive and smooth in (log T, eta);
 * node states along a collapse-shaped profile: rho from 3e14 g/cm^3 at 10 km
   to 1e9 g/cm^3 at 3000 km, T = 40 MeV (r/10 km)^-0.647, Ye from 0.25 to 0.5,
-  and occupations of logistic shape with seeded perturbations.
+  and occupations of logistic shape with seeded perturbations (up to 30%,
+  smaller in the dense core).
 """
 
 import math
@@ -109,7 +110,9 @@ def _occupations(rng, en, ns, rho, T, Ye, amp=0.3):
 
     The guess is the textbook degenerate-electron Fermi energy
     11.1 MeV (rho Ye / 1e10 g cm^-3)^(1/3) lowered by 1.5 T; it only shapes the
-    input spectra and is never used by the solvers.
+    input spectra and is never used by the solvers.  Each energy bin is
+    perturbed by a uniform factor 1 +- amp / (1 + rho / 1e12 g cm^-3): up to 30%
+    in the semi-transparent region, small in the thermalised dense core.
     """
     N = rho.size
     ne = en.size
@@ -118,7 +121,8 @@ def _occupations(rng, en, ns, rho, T, Ye, amp=0.3):
     for s in range(ns):
         a = a_e if s == 0 else (-a_e if s == 1 else np.zeros(N))
         base = _logistic(en[None, :], a[:, None], T[:, None])
-        pert = 1.0 + amp * rng.uniform(-1.0, 1.0, size=(N, ne))
+        a_r = amp / (1.0 + rho / 1e12)
+        pert = 1.0 + a_r[:, None] * rng.uniform(-1.0, 1.0, size=(N, ne))
         D[:, s, :] = np.clip(base * pert, 0.0, 1.0 - 1e-6)
     return D
 

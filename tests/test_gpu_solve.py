@@ -117,13 +117,17 @@ def test_paper_literal_final_state(case2):
         compare_node(out, n, r, g.W2, PARITY)
 
 
-def test_iteration_caps_set_status(case2):
+@pytest.mark.parametrize("caps", [dict(max_inner=1, max_outer=1), dict(max_inner=1, max_outer=5),
+                                  dict(max_inner=3, max_outer=4), dict(max_outer=1), dict(max_outer=2)])
+def test_iteration_caps_set_status(case2, caps):
     edges, g, tables, inp, ctx = case2
-    out = gpu_solve(ctx, inp, max_inner=1, max_outer=1)
-    ref = _oracle(g, tables, inp, [0, 3], max_inner=1, max_outer=1)
-    for n, r in zip([0, 3], ref):
+    caps = dict(caps, tol_inner=1e-13, tol_outer=1e-13)
+    out = gpu_solve(ctx, inp, **caps)
+    nodes = [0, 3, 17]
+    ref = _oracle(g, tables, inp, nodes, **caps)
+    for n, r in zip(nodes, ref):
         assert out["status"][n] == r["status"]
-        assert out["n_inner"][n] == 1 and out["n_outer"][n] == 1
+        assert out["n_inner"][n] == r["n_inner"] and out["n_outer"][n] == r["n_outer"]
         compare_node(out, n, r, g.W2, 1e-10)
 
 
