@@ -45,6 +45,8 @@ def _args():
     ap.add_argument("--impl", default="nmc", choices=["nmc", "reference"])
     ap.add_argument("--nodes", type=int, default=N_NODES)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                    help="path reported as the headline value (both are timed)")
     return ap.parse_args()
 
 
@@ -169,6 +171,30 @@ def cpu_baseline(edges, tables, inp):
             "sample": f"first {CPU_SAMPLE} nodes of the workload, numpy FP64 oracle, one thread, {dt:.1f} s"}
 
 
+FP32_PEAK_TFLOPS = 80.6   # dense FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (recipe unit count and clock)
+MIXED_TOL = (1e-6, 1e-7)  # inner, outer tolerances reachable in FP32
+
+
+def _time_path(ctx, prm, t, out, steps, warmup, barrier, stream):
+    import torch
+
+    def step():
+        ctx.collision_solve(prm, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"], out=out)
+
+    for _ in range(warmup):
+        step()
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    barrier()
+    per_step = [a.elapsed_time(b) for a, b in evs]
+    total_ms = evs[0][0].elapsed_time(evs[-1][1])
+    return per_step, total_ms
+
+
 def run_nmc(args):
     import torch
     from paper_2601_00976_gb300 import nmc, flops
@@ -181,12 +207,12 @@ def run_nmc(args):
     edges, eps, tables, inp = _workload(rank, args.nodes)
     ctx = nmc.Context(edges, NQ, NS, tables)
     t = {k: torch.tensor(v, device=dev) for k, v in inp.items()}
-    prm = nmc.default_params(tol_inner=TOL, tol_outer=TOL, m_inner=MEM, m_outer=MEM)
-    out = ctx.collision_solve(prm, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
     stream = torch.cuda.current_stream()
-
-    def step():
-        ctx.collision_solve(prm, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"], out=out)
+    p64 = nmc.default_params(tol_inner=TOL, tol_outer=TOL, m_inner=MEM, m_outer=MEM)
+    pmx = nmc.default_params(tol_inner=MIXED_TOL[0], tol_outer=MIXED_TOL[1], m_inner=MEM, m_outer=MEM,
+                             precision=nmc.MIXED)
+    o64 = ctx.collision_solve(p64, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+    omx = ctx.collision_solve(pmx, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
 
     def barrier():
         torch.cuda.synchronize()
@@ -194,73 +220,103 @@ def run_nmc(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
-    clk = ClockSampler(dev.index)
-    clk.start()
-    time.sleep(0.3)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        evs[k][0].record(stream)
-        step()
-        evs[k][1].record(stream)
-    barrier()
-    clk.stop()
-    per_step = [a.elapsed_time(b) for a, b in evs]
-    total_ms = evs[0][0].elapsed_time(evs[-1][1])
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev)
+    def allmax(x):
+        if ws == 1:
+            return x
+        tt = torch.tensor([x], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = tt.item()
-    n_in = out["n_inner"].cpu().numpy().astype(np.int64)
-    n_out = out["n_outer"].cpu().numpy().astype(np.int64)
-    status = out["status"].cpu().numpy()
-    fl = float(np.sum(flops.node_flops(NS, len(eps), N_ELEM, NQ, MEM, n_in, n_out)))
-    kern_ms = statistics.mean(per_step)
-    achieved = fl / (kern_ms * 1e-3) / 1e12
+        return tt.item()
 
+    def allsum(x):
+        if ws == 1:
+            return x
+        tt = torch.tensor([x], device=dev, dtype=torch.int64)
+        torch.distributed.all_reduce(tt)
+        return int(tt.item())
+
+    headline_mixed = args.precision == "mixed"
+    clk = ClockSampler(dev.index)
+    res = {}
+    for name, prm, out in (("fp64", p64, o64), ("mixed", pmx, omx)):
+        if name == ("mixed" if headline_mixed else "fp64"):
+            clk.start()
+            time.sleep(0.3)
+        per_step, total_ms = _time_path(ctx, prm, t, out, args.steps, args.warmup, barrier, stream)
+        if name == ("mixed" if headline_mixed else "fp64"):
+            clk.stop()
+        n_in = out["n_inner"].cpu().numpy().astype(np.int64)
+        n_out = out["n_outer"].cpu().numpy().astype(np.int64)
+        status = out["status"].cpu().numpy()
+        fl = float(np.sum(flops.node_flops(NS, len(eps), N_ELEM, NQ, MEM, n_in, n_out)))
+        kern_ms = statistics.mean(per_step)
+        res[name] = dict(total_ms=allmax(total_ms), kern_ms=kern_ms, flops=fl, n_in=n_in, n_out=n_out,
+                         converged=allsum(int(np.count_nonzero(status == 0))), flagged=int(np.count_nonzero(status)))
+
+    # accuracy of the mixed path against the FP64 path on the same inputs
+    ok = ((o64["status"] == 0) & (omx["status"] == 0)).cpu().numpy()
+    wt = torch.tensor(ctx.w2, device=dev)
+    ref = torch.sqrt(torch.sum(wt * o64["J"] ** 2, dim=-1))
+    errD = (torch.sqrt(torch.sum(wt * (omx["J"] - o64["J"]) ** 2, dim=-1)) / ref).cpu().numpy()   # (n, species)
+    thick = inp["rho"] >= 1e12
+    err = {"D_wnorm_by_species": [float(x) for x in errD[ok].max(axis=0)],
+           "D_wnorm_by_species_rho_below_1e12": [float(x) for x in errD[ok & ~thick].max(axis=0)]}
+    for k in ("Ye", "eps", "T"):
+        err[k] = float((torch.abs(omx[k] - o64[k]) / torch.abs(o64[k])).cpu().numpy()[ok].max())
+
+    head = res["mixed" if headline_mixed else "fp64"]
+    hprm = pmx if headline_mixed else p64
     # end to end through the public API with pinned host buffers
     host = {k: torch.tensor(v).pin_memory() for k, v in inp.items()}
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    d2h = sum(v.numel() * v.element_size() for v in o64.values())
     barrier()
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ctx.collision_solve(prm, host["rho"], host["T"], host["Ye"], host["D"], host["I"], host["dt"], host["scale"])
+        ctx.collision_solve(hprm, host["rho"], host["T"], host["Ye"], host["D"], host["I"], host["dt"], host["scale"])
     barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = allmax((time.perf_counter() - t0) / e2e_steps)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(edges, tables, inp)
-    converged = int(np.count_nonzero(status == 0))
-    if ws > 1:
-        cc = torch.tensor([converged], device=dev, dtype=torch.int64)
-        torch.distributed.all_reduce(cc)
-        converged = int(cc.item())
     if rank == 0:
-        # converged solves only: a node that stopped at an iteration cap is not counted
-        value = converged * args.steps / (total_ms * 1e-3)
-        clocks = clk.summary()
+        def line_value(r):
+            return r["converged"] * args.steps / (r["total_ms"] * 1e-3)
+
+        def roof(r, peak, kernel, note):
+            ach = r["flops"] / (r["kern_ms"] * 1e-3) / 1e12
+            return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": None, "kernel": kernel, "peak_source": note,
+                    "algorithmic_flops_per_launch": r["flops"], "kernel_ms": r["kern_ms"]}
+
+        r64, rmx = res["fp64"], res["mixed"]
+        roof64 = roof(r64, FP64_PEAK_TFLOPS, "fused_kernel<double>", "derived FP64 FMA rate at 2.07 GHz")
+        roofmx = roof(rmx, FP32_PEAK_TFLOPS, "fused_kernel<float>",
+                      "derived FP32 FMA rate at 2.07 GHz; the path also issues FP64 least-squares/EoS work")
+        value = line_value(head)
         line = {
-            "metric": "converged collision solves/s (nodes*steps/s), FP64", "value": value, "unit": "solves/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes_per_gpu": args.nodes, "l2": "inputs_larger_than_l2",
-                       "mean_inner_iters": float(n_in.mean()), "mean_outer_iters": float(n_out.mean()),
-                       "max_inner_iters": int(n_in.max()), "nodes_flagged": int(np.count_nonzero(status)),
-                       "converged_fraction": converged / (ws * args.nodes)},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": "fused_fp64_kernel", "peak_source": "derived FP64 FMA rate at 2.07 GHz",
-                         "algorithmic_flops_per_launch": fl, "kernel_ms": kern_ms},
-            "e2e": {"value": ws * converged / (ws * args.nodes) * args.nodes / e2e_s, "unit": "solves/s",
-                    "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+            "metric": "converged collision solves/s (nodes*steps/s), mixed vs FP64 at stated error",
+            "value": value, "unit": "solves/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["total_ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if headline_mixed else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("FP64, ", ""), "precision": args.precision,
+                       "nodes_per_gpu": args.nodes, "l2": "inputs_larger_than_l2",
+                       "tolerances": {"fp64": [TOL, TOL], "mixed": list(MIXED_TOL)},
+                       "fp64_solves_per_s": line_value(r64), "mixed_solves_per_s": line_value(rmx),
+                       "speedup_mixed_vs_fp64": line_value(rmx) / line_value(r64),
+                       "mixed_max_rel_error_vs_fp64": err,
+                       "mean_inner_iters": float(head["n_in"].mean()), "mean_outer_iters": float(head["n_out"].mean()),
+                       "max_inner_iters": int(head["n_in"].max()), "nodes_flagged": head["flagged"],
+                       "converged_fraction": head["converged"] / (ws * args.nodes)},
+            "roofline": roofmx if headline_mixed else roof64,
+            "roofline_fp64": roof64,
+            "roofline_mixed": roofmx,
+            "e2e": {"value": ws * args.nodes * head["converged"] / (ws * args.nodes) / e2e_s, "unit": "solves/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": args.steps,
-            "clocks": clocks,
+            "clocks": clk.summary(),
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu

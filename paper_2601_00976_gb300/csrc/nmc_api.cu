@@ -94,6 +94,12 @@ int upload(nmc_ctx* ctx, const T* host, size_t count, const T** dev) {
     return NMC_OK;
 }
 
+int upload_f32(nmc_ctx* ctx, const double* host, size_t count, double scale, const float** dev) {
+    std::vector<float> tmp(count);
+    for (size_t i = 0; i < count; ++i) tmp[i] = (float)(host[i] * scale);
+    return upload(ctx, tmp.data(), count, dev);
+}
+
 Axis make_axis(double lo, double hi, int n) {
     Axis a;
     a.lo = lo;
@@ -271,8 +277,17 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
         g.ends[0][p] = p < nq ? lagrange(xi, p, -0.5) : 0.0;
         g.ends[1][p] = p < nq ? lagrange(xi, p, 0.5) : 0.0;
     }
+    std::vector<double> wt(ne);
+    double sum_wt = 0.0;
+    for (int q = 0; q < ne; ++q) { wt[q] = ctx->w2[q] / kCW; sum_wt += wt[q]; }
+    g.sum_wt = sum_wt;
     int rc = NMC_OK;
     if (rc == NMC_OK) rc = upload(ctx, ctx->eps.data(), ne, &g.eps);
+    if (rc == NMC_OK) rc = upload(ctx, wt.data(), ne, &g.wt);
+    if (rc == NMC_OK) rc = upload_f32(ctx, wt.data(), ne, 1.0, &g.wt_f);
+    if (rc == NMC_OK) rc = upload_f32(ctx, pe.data(), pe.size(), 1.0, &g.proj_e_f);
+    if (rc == NMC_OK) rc = upload_f32(ctx, pc.data(), pc.size(), 1.0, &g.proj_c_f);
+    if (rc == NMC_OK) rc = upload_f32(ctx, pa.data(), pa.size(), 1.0, &g.proj_a_f);
     if (rc == NMC_OK) rc = upload(ctx, ctx->w2.data(), ne, &g.w2);
     if (rc == NMC_OK) rc = upload(ctx, ctx->w3.data(), ne, &g.w3);
     if (rc == NMC_OK) rc = upload(ctx, lneps.data(), ne, &g.lneps);
@@ -294,6 +309,11 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
     if (rc == NMC_OK) rc = upload(ctx, tb->iso, n_op, &t.iso);
     if (rc == NMC_OK) rc = upload(ctx, tb->nes, n_nes, &t.nes);
     if (rc == NMC_OK) rc = upload(ctx, tb->pair, n_pair, &t.pair);
+    // FP32 copies for the mixed path; kernel tables prescaled by 4 pi / (hc)^3
+    if (rc == NMC_OK) rc = upload_f32(ctx, tb->emab, n_op, 1.0, &t.emab_f);
+    if (rc == NMC_OK) rc = upload_f32(ctx, tb->iso, n_op, 1.0, &t.iso_f);
+    if (rc == NMC_OK) rc = upload_f32(ctx, tb->nes, n_nes, kCW, &t.nes_f);
+    if (rc == NMC_OK) rc = upload_f32(ctx, tb->pair, n_pair, kCW, &t.pair_f);
     if (rc == NMC_OK) {
         void* p = nullptr;
         e = cudaMalloc(&p, 256);
@@ -352,8 +372,6 @@ int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n, const dou
     if (!rho || !T_in || !Ye_in || !J_in || !H_in || !dt || !J_out || !H_out || !Ye_out || !eps_out ||
         !T_out || !n_outer || !n_inner || !status)
         return set_error(ctx, NMC_EINVAL, "null array argument");
-    if (params->precision != NMC_FP64)
-        return set_error(ctx, NMC_EUNSUPPORTED, "mixed precision is not available in this build");
     if (params->mode != NMC_MODE_FUSED)
         return set_error(ctx, NMC_EUNSUPPORTED, "plain mode is not available in this build");
     SolveArgs a{};
@@ -365,7 +383,7 @@ int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n, const dou
     a.J_out = J_out; a.H_out = H_out; a.Ye_out = Ye_out; a.eps_out = eps_out; a.T_out = T_out;
     a.n_outer = n_outer; a.n_inner = n_inner; a.status = status;
     a.queue = ctx->queue;
-    return launch_fused_fp64(ctx, a, static_cast<cudaStream_t>(stream));
+    return launch_fused(ctx, a, static_cast<cudaStream_t>(stream));
 }
 
 int opacity_interp(nmc_ctx* ctx, int32_t which, int32_t species, int64_t p, const double* rho,

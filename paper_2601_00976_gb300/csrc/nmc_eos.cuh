@@ -73,4 +73,76 @@ __device__ __forceinline__ double eos_mu_hat(double T, double Ye) {
     return T * log((1.0 - Ye) / Ye) + kDmNP;
 }
 
+// ---- FP32 variants for the mixed-precision path ----
+// Densities are carried times (hbar c)^3 (MeV^3) and energy densities times
+// (hbar c)^3 (MeV^4), so every intermediate stays inside FP32 range:
+// u (hbar c)^3 = 7 pi^2 T^4/60 + T^2 mu^2/2 + mu^4/(4 pi^2) + 1.5 T nb + pi^2 T^4/15.
+
+struct EosScaleF {
+    float nb;      // (rho / m_B) (hbar c)^3
+    float ne;      // Ye nb
+    double k;      // eps [erg/g] = u~ [MeV^4] * k,  k = MeV/erg / ((hbar c)^3 rho)
+};
+
+__device__ __forceinline__ EosScaleF eos_scale(double rho, double Ye) {
+    const double hc3 = kHbarC * kHbarC * kHbarC;
+    EosScaleF s;
+    const double nb = rho / kMB * hc3;
+    s.nb = (float)nb;
+    s.ne = (float)(Ye * nb);
+    s.k = kMeVErg / (hc3 * rho);
+    return s;
+}
+
+__device__ __forceinline__ float eos_mu_e_f(float ne, float T) {
+    const float pi2 = (float)(kPi * kPi);
+    const float p = pi2 * T * T;
+    const float q = -3.0f * pi2 * ne;
+    return -2.0f * sqrtf(p / 3.0f) * sinhf(asinhf(1.5f * q / p * sqrtf(3.0f / p)) / 3.0f);
+}
+
+__device__ __forceinline__ void eos_u_f(const EosScaleF& sc, float T, float* u, float* du) {
+    const float pi2 = (float)(kPi * kPi);
+    const float mu = eos_mu_e_f(sc.ne, T);
+    const float T2 = T * T, mu2 = mu * mu;
+    *u = 7.0f * pi2 * T2 * T2 / 60.0f + 0.5f * T2 * mu2 + mu2 * mu2 / (4.0f * pi2) + 1.5f * T * sc.nb +
+         pi2 / 15.0f * T2 * T2;
+    const float dmu = -2.0f * pi2 * T * mu / (3.0f * mu2 + pi2 * T2);
+    *du = 7.0f * pi2 * T2 * T / 15.0f + T * mu2 + (T2 * mu + mu2 * mu / pi2) * dmu + 1.5f * sc.nb +
+          4.0f * pi2 / 15.0f * T2 * T;
+}
+
+// Temperature for the mixed path: bracketed Newton in FP32 to ~1e-7, then one
+// FP64 Newton step on eps(rho, T, Ye), which squares the relative error.
+__device__ double eos_temperature_mixed(double rho, double eps_t, double Ye, double T0, bool* ok) {
+    *ok = true;
+    if (!(Ye > 0.0 && Ye < 1.0) || !isfinite(eps_t)) {
+        *ok = false;
+        return isfinite(T0) ? T0 : 1.0;
+    }
+    const EosScaleF sc = eos_scale(rho, Ye);
+    const float ut = (float)(eps_t / sc.k);
+    float lo = (float)kTMin, hi = (float)kTMax, u, du;
+    eos_u_f(sc, lo, &u, &du);
+    if (ut <= u) { *ok = false; return kTMin; }
+    eos_u_f(sc, hi, &u, &du);
+    if (ut >= u) { *ok = false; return kTMax; }
+    float T = (T0 > kTMin && T0 < kTMax) ? (float)T0 : sqrtf(lo * hi);
+    for (int it = 0; it < 100; ++it) {
+        eos_u_f(sc, T, &u, &du);
+        const float f = u - ut;
+        if (f > 0.0f) hi = T; else lo = T;
+        if (f == 0.0f) break;
+        float Tn = T - f / du;
+        if (!(Tn > lo && Tn < hi)) Tn = 0.5f * (lo + hi);
+        const float d = fabsf(Tn - T);
+        T = Tn;
+        if (d <= 2e-7f * T || hi - lo <= 4e-7f * hi) break;
+    }
+    double Td = T, e, de;
+    eos_eps(rho, Td, Ye, &e, &de);
+    const double Tn = Td - (e - eps_t) / de;
+    return (Tn > kTMin && Tn < kTMax) ? Tn : Td;
+}
+
 }  // namespace nmc

@@ -29,6 +29,7 @@ constexpr double kMeVErg = 1.602176634e-6;         // erg/MeV
 constexpr double kDmNP = 1.2933;                   // MeV
 constexpr double kTMin = 1.0e-3;                   // MeV, EoS range
 constexpr double kTMax = 1.0e3;
+constexpr double kCW = 4.0 * kPi / (kHC * kHC * kHC);   // 4 pi / (hc)^3  [cm^-3 MeV^-3]
 
 // Uniform table axis: value v maps to x = (v - lo) * inv_d with cell floor(x).
 struct Axis {
@@ -46,8 +47,15 @@ struct DevGrid {
     const double* proj_e;  // [n_elem][Q] quadrature energies
     const double* proj_c;  // [n_elem][nq][Q] projection operator (mass^-1 * basis * weights)
     const double* proj_a;  // [n_elem][Q] eps^2-weighted cell-average weights
+    const double* wt;      // [ne] W2 / (4 pi / (hc)^3) = w eps^2 Delta eps  [MeV^3]
+    // FP32 copies for the mixed-precision kernel
+    const float* proj_e_f;
+    const float* proj_c_f;
+    const float* proj_a_f;
+    const float* wt_f;
     double ends[2][kMaxNq];  // ell_p(-1/2), ell_p(+1/2)
     double sum_w2;
+    double sum_wt;
 };
 
 struct DevTables {
@@ -56,6 +64,11 @@ struct DevTables {
     const double* iso;
     const double* nes;     // [ns][nkt][neta][ne][ne]
     const double* pair;    // [ns/2][nkt][neta][ne][ne]
+    // FP32 copies for the mixed-precision kernel; kernels prescaled by 4 pi / (hc)^3
+    const float* emab_f;
+    const float* iso_f;
+    const float* nes_f;
+    const float* pair_f;
 };
 
 struct SolveArgs {
@@ -79,7 +92,7 @@ struct SolveArgs {
     int32_t* n_inner;
     uint32_t* status;
     int* queue;
-    // shared-memory carve (offsets in doubles)
+    // shared-memory carve (byte offsets)
     int off_phi, off_ann, off_vec, off_red, off_node;
 };
 
@@ -101,10 +114,10 @@ struct nmc_ctx {
 
 namespace nmc {
 // launchers (nmc_solve.cu, nmc_interp.cu)
-int launch_fused_fp64(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream);
+int launch_fused(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream);
 int launch_opacity_interp(nmc_ctx* ctx, int which, int species, long long p, const double* rho,
                           const double* T, const double* Ye, const double* E, double* out,
                           cudaStream_t stream);
-size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, SolveArgs* a);
+size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, bool mixed, SolveArgs* a);
 int set_error(nmc_ctx* ctx, int code, const std::string& msg);
 }  // namespace nmc

@@ -1,35 +1,46 @@
-// Fused, persistent FP64 kernel for the implicit neutrino--matter collision
-// solve (Sec. 3.5, Algorithm 1 with Algorithms 2 and 3).
+// Fused, persistent kernel for the implicit neutrino--matter collision solve
+// (Sec. 3.5, Algorithm 1 with Algorithms 2 and 3), in two precisions:
+//   R = double  every step in FP64;
+//   R = float   mixed: table interpolation, D^Eq, kernel contractions and the
+//               fixed-point sweeps (map Q, residuals, Anderson mixing, Gram
+//               sums, Algorithm 2) in FP32; conservation sums, matter update,
+//               the Anderson least-squares solves and the final EoS step in FP64.
 //
 // Mapping.  One thread block solves one spatial node at a time; blocks are
 // persistent and take node indices from a device work queue (an atomic
 // counter), so nodes with many iterations do not hold up others.  Inside a
 // block, thread (s, q) owns species s at energy node q: its moments
-// (D, I^1, I^2, I^3), old moments, opacities, and its slice of the Anderson
+// (D, I^1, I^2, I^3), old moments, opacities and its slice of the Anderson
 // history (registers).  The node's NES kernels Phi_Out[s] (one ne x ne matrix
 // per species) and pair kernels Phi_Ann[p] (one per particle/antiparticle
 // pair) live in shared memory, rows padded to ne + 1 so that both row- and
 // column-wise reads are free of bank conflicts.
 //
-// Per outer iteration (ComputeOpacities of Alg. 1): EoS -> chemical
-// potentials (thread 0); Fermi--Dirac values at the projection quadrature
-// points (all threads), eps^2-weighted projection and bound limiter per
-// (species, element) (Eq. fermiDiracProjection); trilinear log-table
-// interpolation of chi_EmAb and sigma_Iso with coalesced rows of ne energies;
-// bilinear (log10 T, eta) interpolation of the kernel tables into shared
-// memory, then the NES up-scattering triangle by detailed balance
-// (Eqs. inOutInvarianceNES, detailedBalanceNES).
+// Scaling.  Rates are formed as dimensionless products: matrices hold
+// K = dtau * (4 pi / (hc)^3) * Phi and vectors hold W~ D with
+// W~_q = w_q eps_q^2 Delta eps_e = W2_q / (4 pi / (hc)^3), so that
+// sum_q' K W~ D = dtau * (rate of Eqs. nesRatesNodal / pairRatesNodal);
+// chi_EmAb and sigma_Iso are carried as dtau * chi.  Every intermediate is
+// O(1e-30 .. 1e8), inside FP32 range.
 //
-// Per inner iteration: rates as shared-memory mat-vecs (Eqs. nesRatesNodal,
-// pairRatesNodal; Phi_In = Phi_Out^T, the antiparticle's Phi_Ann is the
-// transpose, Phi_Pro = a_s(q) a_sbar(q') Phi_Ann with a = D/(1-D) by
-// Eq. detailedBalancePair), the map Q (Eq. implicitMomentsNodal, v = 0), one
-// block reduction for the new row of the Anderson Gram matrix, a tiny FP64
-// least-squares solve in thread 0, the mixing update, and a per-species
-// reduction for Algorithm 2.
+// Per outer iteration (ComputeOpacities of Alg. 1): EoS -> chemical
+// potentials; Fermi--Dirac values at the projection quadrature points (all
+// threads), eps^2-weighted projection and bound limiter per (species, element)
+// (Eq. fermiDiracProjection); trilinear log-table interpolation of chi_EmAb and
+// sigma_Iso with coalesced rows of ne energies; bilinear (log10 T, eta)
+// interpolation of the kernel tables into shared memory, then the NES
+// up-scattering triangle by detailed balance (Eqs. inOutInvarianceNES,
+// detailedBalanceNES).
+//
+// Per inner iteration: rates as shared-memory mat-vecs (Phi_In = Phi_Out^T;
+// the antiparticle's Phi_Ann is the transpose; Phi_Pro = a_s(q) a_sbar(q')
+// Phi_Ann with a = D/(1-D) by Eq. detailedBalancePair), the map Q
+// (Eq. implicitMomentsNodal, v = 0), one block reduction for the new row of the
+// Anderson Gram matrix, the least-squares solve in thread 0 (FP64), the mixing
+// update, and a per-species reduction for Algorithm 2.
 //
 // Matter update (Eq. implicitFluidNodal with Eqs. eulerianEnergyLG,
-// eulerianNumberLG): one block reduction for E_nu and N_nu, the outer
+// eulerianNumberLG): one FP64 block reduction for E_nu and N_nu, the outer
 // Anderson step and Algorithm 3 in thread 0, then T by EoS root finding.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -43,6 +54,15 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+__device__ __forceinline__ double r_exp(double x) { return exp(x); }
+__device__ __forceinline__ float r_exp(float x) { return expf(x); }
+__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double r_log10(double x) { return log10(x); }
+__device__ __forceinline__ float r_log10(float x) { return log10f(x); }
+
 template <int MAXM>
 struct NodeShared {
     double rho, dtau, T, eta_e;
@@ -53,20 +73,21 @@ struct NodeShared {
     double qh[kMaxOuterMem][2], fh[kMaxOuterMem][2];
     double G[MAXM][MAXM];
     double alpha[MAXM];
+    float alpha_f[MAXM];
     double dnorm[kMaxSpecies];
     double sp_out[kMaxSpecies * 4];
     double blk_out[8];
-    // table cells
     double tr, tt, ty, kt, ke;
     int ir, it, iy, ikt, ike;
     long long node;
-    int status, n_inner, n_outer, nho;
+    int status, n_inner, n_outer;
     int conv_in, conv_out, bad, done;
 };
 
-// Sum K values over the whole block; result in out[0..K) for every thread.
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* red, double* out) {
+// Sum K values over the whole block; result in out[0..K).
+template <int K, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[K], void* scratch, T* out) {
+    T* red = static_cast<T*>(scratch);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
@@ -80,7 +101,7 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* red, double* o
     __syncthreads();
     if (threadIdx.x < K) {
         const int nw = blockDim.x >> 5;
-        double s = 0.0;
+        T s = 0;
         for (int i = 0; i < nw; ++i) s += red[i * K + threadIdx.x];
         out[threadIdx.x] = s;
     }
@@ -89,8 +110,9 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* red, double* o
 
 // Sum K values over each species group (threads s*nep .. s*nep+nep-1);
 // result in out[s*K + k].  nep is a power of two <= 32 or a multiple of 32.
-template <int K>
-__device__ __forceinline__ void species_sum(double (&v)[K], double* red, double* out, int nep, int ns) {
+template <int K, typename T>
+__device__ __forceinline__ void species_sum(T (&v)[K], void* scratch, T* out, int nep, int ns) {
+    T* red = static_cast<T*>(scratch);
     const int W = nep < 32 ? nep : 32;
     for (int off = W >> 1; off > 0; off >>= 1) {
 #pragma unroll
@@ -115,7 +137,7 @@ __device__ __forceinline__ void species_sum(double (&v)[K], double* red, double*
         const int wps = nep >> 5;
         if (tid < ns * K) {
             const int sp = tid / K, k = tid % K;
-            double s = 0.0;
+            T s = 0;
             for (int i = 0; i < wps; ++i) s += red[(sp * wps + i) * K + k];
             out[sp * K + k] = s;
         }
@@ -181,23 +203,25 @@ __device__ void outer_anderson(const double (&fh)[kMaxOuterMem][2], int m, doubl
     anderson_solve<MM>(G, m, beta);
 }
 
-__device__ __forceinline__ void axis_cell(double v, const Axis& ax, int* i, double* t, int* clamped) {
-    double x = (v - ax.lo) * ax.inv_d;
-    if (!(x >= 0.0)) { if (!(x == x) || x < 0.0) *clamped = 1; x = 0.0; }
-    if (x > ax.n - 1) { x = ax.n - 1; *clamped = 1; }
-    int c = (int)floor(x);
+template <typename R>
+__device__ __forceinline__ void axis_cell(R v, const Axis& ax, int* i, double* t, int* clamped) {
+    R x = (v - (R)ax.lo) * (R)ax.inv_d;
+    if (!(x >= (R)0)) { *clamped = 1; x = 0; }
+    if (x > (R)(ax.n - 1)) { x = (R)(ax.n - 1); *clamped = 1; }
+    int c = (int)floor((double)x);
     if (c > ax.n - 2) c = ax.n - 2;
     *i = c;
-    *t = x - c;
+    *t = (double)(x - (R)c);
 }
 
 }  // namespace
 
 // MAXT: block-size class (threads = ns * nep rounded up to 32 must not exceed
 // it); MINB blocks per SM cap registers at 128 per thread in every class.
-template <int MAXM, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs a) {
-    extern __shared__ __align__(16) double sm[];
+template <typename R, int MAXM, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
+    constexpr bool kMixed = sizeof(R) == 4;
+    extern __shared__ __align__(16) unsigned char smb[];
     const DevGrid& g = a.g;
     const int NS = g.ns, NE = g.ne, NEP = g.nep, LD = g.ld;
     const int tid = threadIdx.x;
@@ -205,17 +229,18 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
     const bool act = (s < NS) && (q < NE);
     const int sq = s * NEP + q;
 
-    double* phi = sm + a.off_phi;        // [NS][NE][LD]   Phi_Out per species
-    double* ann = sm + a.off_ann;        // [NS/2][NE][LD] Phi_Ann per pair (particle)
-    double* vWD = sm + a.off_vec;        // [NS][NEP]  W2 D
-    double* vW1D = vWD + NS * NEP;       //            W2 (1 - D)
-    double* vAW1D = vW1D + NS * NEP;     //            a W2 (1 - D)
-    double* vA = vAW1D + NS * NEP;       //            a = D^Eq / (1 - D^Eq)
-    double* vAi = vA + NS * NEP;         //            1 / a
-    double* vDeq = vAi + NS * NEP;       //            D^Eq
-    double* red = sm + a.off_red;        // reduction scratch
-    NodeShared<MAXM>* nd = reinterpret_cast<NodeShared<MAXM>*>(sm + a.off_node);
-    double* fq = sm + a.off_phi;         // FD values at projection points (reuses phi)
+    R* phi = reinterpret_cast<R*>(smb + a.off_phi);   // [NS][NE][LD]   K_Out per species
+    R* ann = reinterpret_cast<R*>(smb + a.off_ann);   // [NS/2][NE][LD] K_Ann per pair (particle)
+    R* vWD = reinterpret_cast<R*>(smb + a.off_vec);   // [NS][NEP] W~ D
+    R* vW1D = vWD + NS * NEP;                          //           W~ (1 - D)
+    R* vAW1D = vW1D + NS * NEP;                        //           a W~ (1 - D)
+    R* vA = vAW1D + NS * NEP;                          //           a = D^Eq / (1 - D^Eq)
+    R* vAi = vA + NS * NEP;                            //           1 / a
+    R* vDeq = vAi + NS * NEP;                          //           D^Eq
+    R* vDeqc = vDeq + NS * NEP;                        //           1 - D^Eq (mixed)
+    void* red = smb + a.off_red;                       // reduction scratch
+    NodeShared<MAXM>* nd = reinterpret_cast<NodeShared<MAXM>*>(smb + a.off_node);
+    R* fq = phi;                                       // FD values at projection points (reuses phi)
 
     const nmc_params& P = a.p;
     const bool nes_on = (P.proc_mask & NMC_PROC_NES) != 0;
@@ -223,12 +248,20 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
     const double gs = (s == 0) ? 1.0 : (s == 1 ? -1.0 : 0.0);
     const double W2q = act ? g.w2[q] : 0.0;
     const double W3q = act ? g.w3[q] : 0.0;
+    const R Wt = act ? (kMixed ? (R)g.wt_f[q] : (R)g.wt[q]) : (R)0;
+    const double* proj_e = g.proj_e;
+    const double* proj_a = g.proj_a;
+    const double* proj_c = g.proj_c;
 
-    double Fh[MAXM][4], Qh[MAXM][4];
+    // Qh[.][4] holds the complement 1 - Q_D (mixed precision only)
+    R Fh[MAXM][4], Qh[MAXM][5];
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j)
+    for (int j = 0; j < MAXM; ++j) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) { Fh[j][c] = 0.0; Qh[j][c] = 0.0; }
+        for (int c = 0; c < 4; ++c) Fh[j][c] = 0;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) Qh[j][c] = 0;
+    }
 
     for (;;) {
         if (tid == 0) nd->node = atomicAdd(a.queue, 1);
@@ -237,13 +270,13 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
         if (n >= a.n) break;
 
         // ---------------- node set-up ----------------
-        double Ds = 0.0, Is[3] = {0.0, 0.0, 0.0};
+        double Dsd = 0.0, Isd[3] = {0.0, 0.0, 0.0};
         if (act) {
             const long long o = (n * NS + s) * NE + q;
-            Ds = a.J[o];
-            Is[0] = a.H[o * 3 + 0];
-            Is[1] = a.H[o * 3 + 1];
-            Is[2] = a.H[o * 3 + 2];
+            Dsd = a.J[o];
+            Isd[0] = a.H[o * 3 + 0];
+            Isd[1] = a.H[o * 3 + 1];
+            Isd[2] = a.H[o * 3 + 2];
         }
         if (tid == 0) {
             const double rho = a.rho[n], T = a.T[n], Ye = a.Ye[n], dt = a.dt[n];
@@ -262,7 +295,6 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
             nd->y[1] = Ye;
             nd->n_inner = 0;
             nd->n_outer = 0;
-            nd->nho = 0;
             nd->bad = 0;
             nd->done = okin ? 0 : 1;
         }
@@ -270,8 +302,8 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
         if (nd->done) {   // invalid input: outputs = inputs
             if (act) {
                 const long long o = (n * NS + s) * NE + q;
-                a.J_out[o] = Ds;
-                for (int j = 0; j < 3; ++j) a.H_out[o * 3 + j] = Is[j];
+                a.J_out[o] = Dsd;
+                for (int j = 0; j < 3; ++j) a.H_out[o * 3 + j] = Isd[j];
             }
             if (tid == 0) {
                 a.Ye_out[n] = a.Ye[n];
@@ -284,30 +316,45 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
             __syncthreads();
             continue;
         }
-        {   // E_nu*, N_nu* (Eqs. eulerianEnergyLG, eulerianNumberLG at v = 0)
-            double v[2] = {W3q * Ds, gs * W2q * Ds};
-            block_sum<2>(v, red, nd->blk_out);
+        {   // E_nu*, N_nu* in FP64 (Eqs. eulerianEnergyLG, eulerianNumberLG at v = 0)
+            double v[2] = {W3q * Dsd, gs * W2q * Dsd};
+            block_sum<2, double>(v, red, nd->blk_out);
             if (tid == 0) { nd->EN_star[0] = nd->blk_out[0]; nd->EN_star[1] = nd->blk_out[1]; }
         }
-        double M[4] = {Ds, Is[0], Is[1], Is[2]};
-        double chiab = 0.0, sig = 0.0, deq = 0.0;
+        const R Ds = (R)Dsd;
+        const R Dsc = (R)(1.0 - Dsd);   // 1 - D*, formed in FP64
+        const R Is[3] = {(R)Isd[0], (R)Isd[1], (R)Isd[2]};
+        R M[4] = {Ds, Is[0], Is[1], Is[2]};
+        // Mixed precision carries the blocking factor 1 - D as its own iterate:
+        // 1 - D in FP32 loses all digits for degenerate D ~ 1 - 1e-6, and the
+        // pair emissivity multiplies it by a = D^Eq/(1 - D^Eq) ~ 1e6.
+        R Dc = Dsc;
+        R chiab = 0, sig = 0, deq = 0, deqc = 0;
         int outer_exit = 0;
 
         for (int k = 1;; ++k) {
             // ================= ComputeOpacities(y^[k]) =================
             if (tid == 0) {
                 const double T = nd->T, Ye = nd->y[1], rho = nd->rho;
-                const double mu_e = eos_mu_e(rho, T, Ye);
+                double mu_e, mnu;
+                if (kMixed) {
+                    const EosScaleF sc = eos_scale(rho, Ye);
+                    const float mf = eos_mu_e_f(sc.ne, (float)T);
+                    mu_e = mf;
+                    mnu = mf - ((float)T * logf((1.0f - (float)Ye) / (float)Ye) + (float)kDmNP);
+                } else {
+                    mu_e = eos_mu_e(rho, T, Ye);
+                    mnu = mu_e - eos_mu_hat(T, Ye);
+                }
                 nd->eta_e = mu_e / T;
-                const double mnu = mu_e - eos_mu_hat(T, Ye);
                 for (int sp = 0; sp < kMaxSpecies; ++sp) nd->mu[sp] = sp == 0 ? mnu : (sp == 1 ? -mnu : 0.0);
                 int cl = 0;
-                axis_cell(log10(rho), a.tb.rho, &nd->ir, &nd->tr, &cl);
-                axis_cell(log10(T), a.tb.t, &nd->it, &nd->tt, &cl);
-                axis_cell(Ye, a.tb.ye, &nd->iy, &nd->ty, &cl);
+                axis_cell<R>(r_log10((R)rho), a.tb.rho, &nd->ir, &nd->tr, &cl);
+                axis_cell<R>(r_log10((R)T), a.tb.t, &nd->it, &nd->tt, &cl);
+                axis_cell<R>((R)Ye, a.tb.ye, &nd->iy, &nd->ty, &cl);
                 if (nes_on || pair_on) {
-                    axis_cell(log10(T), a.tb.kt, &nd->ikt, &nd->kt, &cl);
-                    axis_cell(nd->eta_e, a.tb.eta, &nd->ike, &nd->ke, &cl);
+                    axis_cell<R>(r_log10((R)T), a.tb.kt, &nd->ikt, &nd->kt, &cl);
+                    axis_cell<R>((R)nd->eta_e, a.tb.eta, &nd->ike, &nd->ke, &cl);
                 }
                 if (cl) nd->status |= NMC_TABLE_CLAMP;
             }
@@ -316,157 +363,231 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
             {
                 const int nqp = g.n_elem * kProjQuad;
                 if (s < NS) {
-                    const double mu = nd->mu[s], Tinv = 1.0 / nd->T;
-                    for (int i = q; i < nqp; i += NEP)
-                        fq[s * nqp + i] = 1.0 / (exp((g.proj_e[i] - mu) * Tinv) + 1.0);
+                    const R mu = (R)nd->mu[s], Tinv = (R)(1.0 / nd->T);
+                    for (int i = q; i < nqp; i += NEP) {
+                        if (kMixed) {   // f and 1 - f from one exp, each without cancellation
+                            const R x = ((R)g.proj_e_f[i] - mu) * Tinv;
+                            const R t = r_exp(-fabsf((float)x));
+                            const R inv = (R)1 / ((R)1 + t);
+                            fq[s * nqp + i] = x > 0 ? t * inv : inv;
+                            fq[(NS + s) * nqp + i] = x > 0 ? inv : t * inv;
+                        } else {
+                            fq[s * nqp + i] = (R)1 / (r_exp(((R)proj_e[i] - mu) * Tinv) + (R)1);
+                        }
+                    }
                 }
                 __syncthreads();
                 // eps^2-weighted projection and bound-enforcing limiter per (species, element)
                 if (s < NS && q < g.n_elem) {
                     const int e = q, nq = g.nq;
-                    const double* f = fq + s * nqp + e * kProjQuad;
-                    const double* pa = g.proj_a + e * kProjQuad;
-                    const double* pc = g.proj_c + e * nq * kProjQuad;
-                    double avg = 0.0, coef[kMaxNq] = {0.0, 0.0, 0.0};
+                    const R* f = fq + s * nqp + e * kProjQuad;
+                    const R* fc = fq + (NS + s) * nqp + e * kProjQuad;
+                    R avg = 0, avgc = 0, coef[kMaxNq] = {0, 0, 0}, coefc[kMaxNq] = {0, 0, 0};
                     for (int gq = 0; gq < kProjQuad; ++gq) {
-                        const double fv = f[gq];
-                        avg += pa[gq] * fv;
-                        for (int pp = 0; pp < nq; ++pp) coef[pp] += pc[pp * kProjQuad + gq] * fv;
+                        const R pa = kMixed ? (R)g.proj_a_f[e * kProjQuad + gq] : (R)proj_a[e * kProjQuad + gq];
+                        const R fv = f[gq];
+                        avg += pa * fv;
+                        R fcv = 0;
+                        if (kMixed) { fcv = fc[gq]; avgc += pa * fcv; }
+                        for (int pp = 0; pp < nq; ++pp) {
+                            const int o = (e * nq + pp) * kProjQuad + gq;
+                            const R pc = kMixed ? (R)g.proj_c_f[o] : (R)proj_c[o];
+                            coef[pp] += pc * fv;
+                            if (kMixed) coefc[pp] += pc * fcv;
+                        }
                     }
-                    const double dmin = P.d_min, dmax = P.d_max;
+                    const R dmin = (R)P.d_min, dmax = (R)P.d_max;
                     if (avg < dmin || avg > dmax) {
-                        const double cv = fmin(fmax(avg, dmin), dmax);
-                        for (int pp = 0; pp < nq; ++pp) coef[pp] = cv;
+                        const bool lo = avg < dmin;
+                        const R cv = lo ? dmin : dmax;
+                        const R cvc = lo ? (R)(1.0 - P.d_min) : (R)(1.0 - P.d_max);
+                        for (int pp = 0; pp < nq; ++pp) { coef[pp] = cv; coefc[pp] = cvc; }
                     } else {
-                        double vmin = coef[0], vmax = coef[0];
+                        R vmin = coef[0], vmax = coef[0];
                         for (int pp = 1; pp < nq; ++pp) { vmin = fmin(vmin, coef[pp]); vmax = fmax(vmax, coef[pp]); }
                         for (int side = 0; side < 2; ++side) {
-                            double v = 0.0;
-                            for (int pp = 0; pp < nq; ++pp) v += coef[pp] * g.ends[side][pp];
+                            R v = 0;
+                            for (int pp = 0; pp < nq; ++pp) v += coef[pp] * (R)g.ends[side][pp];
                             vmin = fmin(vmin, v);
                             vmax = fmax(vmax, v);
                         }
-                        double theta = 1.0;
+                        R theta = 1;
                         if (vmin < dmin) theta = fmin(theta, (avg - dmin) / (avg - vmin));
                         if (vmax > dmax) theta = fmin(theta, (dmax - avg) / (vmax - avg));
-                        for (int pp = 0; pp < nq; ++pp) coef[pp] = avg + theta * (coef[pp] - avg);
+                        for (int pp = 0; pp < nq; ++pp) {
+                            coef[pp] = avg + theta * (coef[pp] - avg);
+                            coefc[pp] = avgc + theta * (coefc[pp] - avgc);
+                        }
                     }
-                    for (int pp = 0; pp < nq; ++pp) vDeq[s * NEP + e * nq + pp] = coef[pp];
+                    for (int pp = 0; pp < nq; ++pp) {
+                        vDeq[s * NEP + e * nq + pp] = coef[pp];
+                        vDeqc[s * NEP + e * nq + pp] = coefc[pp];
+                    }
                 }
                 __syncthreads();
             }
-            // EmAb / Iso: trilinear in (log10 rho, log10 T, Ye) on ln values
+            // EmAb / Iso: trilinear in (log10 rho, log10 T, Ye) on ln values, times dtau
             if (act) {
                 deq = vDeq[sq];
-                vA[sq] = deq / (1.0 - deq);
-                vAi[sq] = (1.0 - deq) / deq;
+                const R dc = kMixed ? vDeqc[sq] : (R)1 - deq;
+                deqc = dc;
+                vA[sq] = deq / dc;
+                vAi[sq] = dc / deq;
                 const int nr = a.tb.rho.n, nt = a.tb.t.n, ny = a.tb.ye.n;
                 const long long base = ((((long long)s * ny + nd->iy) * nt + nd->it) * nr + nd->ir) * NE + q;
                 const long long dR = NE, dT = (long long)nr * NE, dY = (long long)nt * nr * NE;
-                const double tr = nd->tr, tt = nd->tt, ty = nd->ty;
-                double le = 0.0, li = 0.0;
+                const R tr = (R)nd->tr, tt = (R)nd->tt, ty = (R)nd->ty;
+                R le = 0, li = 0;
 #pragma unroll
                 for (int c8 = 0; c8 < 8; ++c8) {
                     const int ca = c8 & 1, cb = (c8 >> 1) & 1, cc = c8 >> 2;
-                    const double w = (ca ? tr : 1.0 - tr) * (cb ? tt : 1.0 - tt) * (cc ? ty : 1.0 - ty);
+                    const R w = (ca ? tr : (R)1 - tr) * (cb ? tt : (R)1 - tt) * (cc ? ty : (R)1 - ty);
                     const long long o = base + ca * dR + cb * dT + cc * dY;
-                    le += w * a.tb.emab[o];
-                    li += w * a.tb.iso[o];
+                    if (kMixed) { le += w * (R)a.tb.emab_f[o]; li += w * (R)a.tb.iso_f[o]; }
+                    else { le += w * (R)a.tb.emab[o]; li += w * (R)a.tb.iso[o]; }
                 }
-                chiab = (P.proc_mask & NMC_PROC_EMAB) ? nd->sc[0] * exp(le) : 0.0;
-                sig = (P.proc_mask & NMC_PROC_ISO) ? nd->sc[1] * exp(li) : 0.0;
+                chiab = (P.proc_mask & NMC_PROC_EMAB) ? (R)(nd->dtau * nd->sc[0]) * r_exp(le) : (R)0;
+                sig = (P.proc_mask & NMC_PROC_ISO) ? (R)(nd->dtau * nd->sc[1]) * r_exp(li) : (R)0;
             }
-            // NES and pair kernels: bilinear in (log10 T, eta_e)
+            // NES and pair kernels: bilinear in (log10 T, eta_e), times dtau 4 pi / (hc)^3
             if (nes_on || pair_on) {
-                const double kt = nd->kt, ke = nd->ke;
-                const double w00 = (1.0 - kt) * (1.0 - ke), w10 = kt * (1.0 - ke);
-                const double w01 = (1.0 - kt) * ke, w11 = kt * ke;
+                const R kt = (R)nd->kt, ke = (R)nd->ke;
+                const R w00 = ((R)1 - kt) * ((R)1 - ke), w10 = kt * ((R)1 - ke);
+                const R w01 = ((R)1 - kt) * ke, w11 = kt * ke;
                 const long long mat = (long long)NE * NE;
                 const long long sE = mat, sT = (long long)a.tb.eta.n * mat;
+                const double unit = kMixed ? nd->dtau : nd->dtau * kCW;   // FP32 tables carry 4 pi/(hc)^3
                 if (nes_on && act) {
-                    const double c = nd->sc[2];
-                    const double* tb = a.tb.nes + (((long long)s * a.tb.kt.n + nd->ikt) * a.tb.eta.n + nd->ike) * mat;
-                    double* P0 = phi + s * NE * LD;
+                    const R c = (R)(unit * nd->sc[2]);
+                    const long long off = (((long long)s * a.tb.kt.n + nd->ikt) * a.tb.eta.n + nd->ike) * mat;
+                    R* P0 = phi + s * NE * LD;
                     for (int r = 0; r < NE; ++r) {   // lower triangle incl. diagonal; row r read coalesced
                         if (q <= r) {
-                            const long long o = (long long)r * NE + q;
-                            P0[r * LD + q] = c * (w00 * tb[o] + w10 * tb[o + sT] + w01 * tb[o + sE] + w11 * tb[o + sT + sE]);
+                            const long long o = off + (long long)r * NE + q;
+                            R v;
+                            if (kMixed) {
+                                const float* tb = a.tb.nes_f;
+                                v = w00 * tb[o] + w10 * tb[o + sT] + w01 * tb[o + sE] + w11 * tb[o + sT + sE];
+                            } else {
+                                const double* tb = a.tb.nes;
+                                v = w00 * tb[o] + w10 * tb[o + sT] + w01 * tb[o + sE] + w11 * tb[o + sT + sE];
+                            }
+                            P0[r * LD + q] = c * v;
                         }
                     }
                 }
                 if (pair_on && s < NS) {
                     const int pr = s >> 1;
-                    const double c = nd->sc[3];
-                    const double* tb = a.tb.pair + (((long long)pr * a.tb.kt.n + nd->ikt) * a.tb.eta.n + nd->ike) * mat;
-                    double* A0 = ann + pr * NE * LD;
+                    const R c = (R)(unit * nd->sc[3]);
+                    const long long off = (((long long)pr * a.tb.kt.n + nd->ikt) * a.tb.eta.n + nd->ike) * mat;
+                    R* A0 = ann + pr * NE * LD;
                     for (int idx = (s & 1) * NEP + q; idx < NE * NE; idx += 2 * NEP) {
                         const int r = idx / NE, cc = idx - r * NE;
-                        const long long o = idx;
-                        A0[r * LD + cc] = c * (w00 * tb[o] + w10 * tb[o + sT] + w01 * tb[o + sE] + w11 * tb[o + sT + sE]);
+                        const long long o = off + idx;
+                        R v;
+                        if (kMixed) {
+                            const float* tb = a.tb.pair_f;
+                            v = w00 * tb[o] + w10 * tb[o + sT] + w01 * tb[o + sE] + w11 * tb[o + sT + sE];
+                        } else {
+                            const double* tb = a.tb.pair;
+                            v = w00 * tb[o] + w10 * tb[o + sT] + w01 * tb[o + sE] + w11 * tb[o + sT + sE];
+                        }
+                        A0[r * LD + cc] = c * v;
                     }
                 }
                 __syncthreads();
-                if (nes_on && act) {   // up-scattering by detailed balance: Phi[r][q] = a_q / a_r Phi[q][r], r < q
-                    double* P0 = phi + s * NE * LD;
-                    const double aq = vA[sq];
+                if (nes_on && act) {   // up-scattering by detailed balance: K[r][q] = a_q / a_r K[q][r], r < q
+                    R* P0 = phi + s * NE * LD;
+                    const R aq = vA[sq];
                     for (int r = 0; r < q; ++r) P0[r * LD + q] = aq * vAi[s * NEP + r] * P0[q * LD + r];
                 }
             }
-            // reference norm ||D^[k,1]||_W2 per species (Algorithm 2 input)
+            // reference norm ||D^[k,1]||_W per species (Algorithm 2 input)
             {
-                double v[1] = {W2q * M[0] * M[0]};
-                species_sum<1>(v, red, nd->sp_out, NEP, NS);
+                R v[1] = {Wt * M[0] * M[0]};
+                R* out = reinterpret_cast<R*>(nd->sp_out);
+                species_sum<1, R>(v, red, out, NEP, NS);
                 if (tid == 0) {
-                    const double fl = P.norm_floor * sqrt(g.sum_w2);
-                    for (int sp = 0; sp < NS; ++sp) nd->dnorm[sp] = fmax(sqrt(nd->sp_out[sp]), fl);
+                    const double fl = P.norm_floor * sqrt(g.sum_wt);
+                    for (int sp = 0; sp < NS; ++sp) nd->dnorm[sp] = fmax((double)r_sqrt(out[sp]), fl);
                 }
             }
             // ================= inner loop =================
-            const double dtau = nd->dtau;
             for (int ell = 1;; ++ell) {
                 if (act) {
-                    vWD[sq] = W2q * M[0];
-                    vW1D[sq] = W2q * (1.0 - M[0]);
-                    vAW1D[sq] = vA[sq] * W2q * (1.0 - M[0]);
+                    const R hole = kMixed ? Dc : (R)1 - M[0];
+                    vWD[sq] = Wt * M[0];
+                    vW1D[sq] = Wt * hole;
+                    vAW1D[sq] = vA[sq] * Wt * hole;
                 }
                 __syncthreads();
-                double F[4] = {0.0, 0.0, 0.0, 0.0}, Qv[4] = {0.0, 0.0, 0.0, 0.0};
+                R F[4] = {0, 0, 0, 0}, Qv[5] = {0, 0, 0, 0, 0};
                 if (act) {
-                    double nin = 0.0, nout = 0.0, pro = 0.0, an = 0.0;
+                    R nin = 0, nout = 0, pro = 0, an = 0;
+                    R cn = 0, cp = 0;   // mixed: net NES / pair terms from pairwise exchanges
                     if (nes_on) {
-                        const double* P0 = phi + s * NE * LD;
-                        const double* x = vWD + s * NEP;
-                        const double* y = vW1D + s * NEP;
-                        for (int j = 0; j < NE; ++j) {
-                            nin = fma(P0[j * LD + q], x[j], nin);    // Phi_In[q][j] = Phi_Out[j][q]
-                            nout = fma(P0[q * LD + j], y[j], nout);
+                        const R* P0 = phi + s * NE * LD;
+                        const R* x = vWD + s * NEP;
+                        const R* y = vW1D + s * NEP;
+                        if (kMixed) {
+                            // exchange j -> q is K[j][q] (u_j v_q), q -> j is K[q][j] (u_q v_j), with
+                            // u = W~ D, v = W~ (1 - D); each product is formed with the same
+                            // operands in the two bins it couples, so the exchanges cancel
+                            // exactly in the number sum and NES conserves number to the
+                            // rounding of the net term (not of the gross rates).
+                            const R uq = x[q], vq = y[q];
+                            for (int j = 0; j < NE; ++j) {
+                                const R kin = P0[j * LD + q], kout = P0[q * LD + j];
+                                nin = r_fma(kin, x[j], nin);        // K_In[q][j] = K_Out[j][q]
+                                nout = r_fma(kout, y[j], nout);
+                                const R e1 = __fmul_rn(kin, __fmul_rn(x[j], vq));
+                                const R e2 = __fmul_rn(kout, __fmul_rn(uq, y[j]));
+                                cn = __fadd_rn(cn, __fsub_rn(e1, e2));
+                            }
+                        } else {
+                            for (int j = 0; j < NE; ++j) {
+                                nin = r_fma(P0[j * LD + q], x[j], nin);    // K_In[q][j] = K_Out[j][q]
+                                nout = r_fma(P0[q * LD + j], y[j], nout);
+                            }
                         }
                     }
                     if (pair_on) {
                         const int pt = s ^ 1;
-                        const double* A0 = ann + (s >> 1) * NE * LD;
-                        const double* x = vAW1D + pt * NEP;
-                        const double* y = vWD + pt * NEP;
-                        if ((s & 1) == 0) {
-                            for (int j = 0; j < NE; ++j) {
-                                const double av = A0[q * LD + j];
-                                pro = fma(av, x[j], pro);
-                                an = fma(av, y[j], an);
-                            }
-                        } else {
-                            for (int j = 0; j < NE; ++j) {
-                                const double av = A0[j * LD + q];
-                                pro = fma(av, x[j], pro);
-                                an = fma(av, y[j], an);
-                            }
+                        const R* A0 = ann + (s >> 1) * NE * LD;
+                        const R* x = vAW1D + pt * NEP;
+                        const R* y = vWD + pt * NEP;
+                        // pair (q, j) is produced at K_Ann (p_q pbar_j), annihilated at
+                        // K_Ann (u_q ubar_j), p = a W~ (1 - D): the same products in the
+                        // particle's and the antiparticle's sums (mixed precision)
+                        const R pq = kMixed ? vAW1D[sq] : (R)0, uq = kMixed ? vWD[sq] : (R)0;
+                        const int stride_j = (s & 1) == 0 ? 1 : LD;
+                        const int base = (s & 1) == 0 ? q * LD : q;
+                        for (int j = 0; j < NE; ++j) {
+                            const R av = A0[base + j * stride_j];
+                            pro = r_fma(av, x[j], pro);
+                            an = r_fma(av, y[j], an);
+                            if (kMixed)
+                                cp = __fadd_rn(cp, __fmul_rn(av, __fsub_rn(__fmul_rn(pq, x[j]), __fmul_rn(uq, y[j]))));
                         }
                         pro *= vA[sq];
                     }
-                    const double eta = chiab * deq + nin + pro;          // Eq. emissivityNodal
-                    const double chi = chiab + nin + nout + pro + an;    // Eq. opacityNodal
-                    const double kap = chi + sig;                        // Eq. transportOpacityNodal
-                    Qv[0] = (Ds + dtau * eta) / (1.0 + dtau * chi);      // Eq. implicitMomentsNodal, v = 0
-                    const double fI = 1.0 / (1.0 + dtau * kap);
+                    const R eta = chiab * deq + nin + pro;          // dtau * Eq. emissivityNodal
+                    const R chi = chiab + nin + nout + pro + an;    // dtau * Eq. opacityNodal
+                    const R kap = chi + sig;                        // dtau * Eq. transportOpacityNodal
+                    if (kMixed) {
+                        // the same map written as Q_D = D + (D* - D + dtau C)/(1 + dtau chi), with the
+                        // net collision term dtau C = dtau (eta - chi D) built from the conservative
+                        // exchange sums; its fixed point does not depend on rounding in chi
+                        const R C = chiab * (deq - M[0]) + (cn + cp) / Wt;
+                        const R inv = (R)1 / ((R)1 + chi);
+                        Qv[0] = M[0] + (Ds - M[0] + C) * inv;
+                        // 1 - Q_D = (1 - D* + dtau (chi - eta))/(1 + dtau chi), formed from positive
+                        // terms each iteration, so the blocking factor carries no accumulated error
+                        Qv[4] = (Dsc + chiab * deqc + nout + an) * inv;
+                    } else {
+                        Qv[0] = (Ds + eta) / ((R)1 + chi);          // Eq. implicitMomentsNodal, v = 0
+                    }
+                    const R fI = (R)1 / ((R)1 + kap);
                     Qv[1] = Is[0] * fI;
                     Qv[2] = Is[1] * fI;
                     Qv[3] = Is[2] * fI;
@@ -474,51 +595,66 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
                     for (int c = 0; c < 4; ++c) F[c] = Qv[c] - M[c];
                 }
 #pragma unroll
-                for (int j = 0; j < MAXM - 1; ++j)
+                for (int j = 0; j < MAXM - 1; ++j) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) { Fh[j][c] = Fh[j + 1][c]; Qh[j][c] = Qh[j + 1][c]; }
+                    if (kMixed) Qh[j][4] = Qh[j + 1][4];
+                }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) { Fh[MAXM - 1][c] = F[c]; Qh[MAXM - 1][c] = Qv[c]; }
+                if (kMixed) Qh[MAXM - 1][4] = Qv[4];
                 const int m = ell < P.m_inner ? ell : P.m_inner;
-                {   // new row of the Gram matrix
-                    double v[MAXM];
+                {   // new row of the Gram matrix; least squares in FP64 (thread 0)
+                    R v[MAXM];
 #pragma unroll
                     for (int j = 0; j < MAXM; ++j)
                         v[j] = F[0] * Fh[j][0] + F[1] * Fh[j][1] + F[2] * Fh[j][2] + F[3] * Fh[j][3];
-                    block_sum<MAXM>(v, red, nd->blk_out);
+                    R* out = reinterpret_cast<R*>(nd->blk_out);
+                    block_sum<MAXM, R>(v, red, out);
                     if (tid == 0) {
                         for (int i = 0; i < MAXM - 1; ++i)
                             for (int j = 0; j < MAXM - 1; ++j) nd->G[i][j] = nd->G[i + 1][j + 1];
                         for (int j = 0; j < MAXM; ++j) {
-                            nd->G[MAXM - 1][j] = nd->blk_out[j];
-                            nd->G[j][MAXM - 1] = nd->blk_out[j];
+                            nd->G[MAXM - 1][j] = (double)out[j];
+                            nd->G[j][MAXM - 1] = (double)out[j];
                         }
                         anderson_solve<MAXM>(nd->G, m, nd->alpha);
+                        for (int j = 0; j < MAXM; ++j) nd->alpha_f[j] = (float)nd->alpha[j];
                     }
                     __syncthreads();
                 }
-                double Mn[4];
+                R Mn[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    double acc = 0.0;
+                    R acc = 0;
 #pragma unroll
                     for (int j = 0; j < MAXM; ++j)
-                        if (j >= MAXM - m) acc = fma(nd->alpha[j], Qh[j][c], acc);   // window only
-                    Mn[c] = act ? acc : 0.0;
+                        if (j >= MAXM - m)   // window only
+                            acc = r_fma(kMixed ? (R)nd->alpha_f[j] : (R)nd->alpha[j], Qh[j][c], acc);
+                    Mn[c] = act ? acc : (R)0;
                 }
-                {   // Algorithm 2: per species, W2-weighted squares of the change per moment
-                    double v[4];
+                R Dcn = Dc;
+                if (kMixed) {
+                    R acc = 0;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) { const double d = Mn[c] - M[c]; v[c] = W2q * d * d; }
+                    for (int j = 0; j < MAXM; ++j)
+                        if (j >= MAXM - m) acc = r_fma((R)nd->alpha_f[j], Qh[j][4], acc);
+                    Dcn = act ? acc : (R)0;
+                }
+                {   // Algorithm 2: per species, W-weighted squares of the change per moment
+                    R v[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) { const R d = Mn[c] - M[c]; v[c] = Wt * d * d; }
                     if (act && !(isfinite(Mn[0]) && isfinite(Mn[1]) && isfinite(Mn[2]) && isfinite(Mn[3])))
                         nd->bad = 1;
-                    species_sum<4>(v, red, nd->sp_out, NEP, NS);
+                    R* out = reinterpret_cast<R*>(nd->sp_out);
+                    species_sum<4, R>(v, red, out, NEP, NS);
                     if (tid == 0) {
                         int conv = 1;
                         for (int sp = 0; sp < NS; ++sp) {
-                            double mx = nd->sp_out[sp * 4];
-                            for (int c = 1; c < 4; ++c) mx = fmax(mx, nd->sp_out[sp * 4 + c]);
-                            if (!(sqrt(mx) <= P.tol_inner * nd->dnorm[sp])) conv = 0;
+                            R mx = out[sp * 4];
+                            for (int c = 1; c < 4; ++c) mx = fmax(mx, out[sp * 4 + c]);
+                            if (!(r_sqrt(mx) <= (R)(P.tol_inner * nd->dnorm[sp]))) conv = 0;
                         }
                         nd->n_inner += 1;
                         if (nd->bad) nd->status |= NMC_NONFINITE;
@@ -529,14 +665,15 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) M[c] = Mn[c];
+                Dc = Dcn;
                 if (nd->conv_in) break;
             }
             // an inner loop stopped at its cap (or a non-finite moment) ends the node
             if (P.frozen_matter || nd->bad || (nd->status & NMC_NOT_CONVERGED_INNER)) { outer_exit = 1; }
-            // ================= matter update (Eq. implicitFluidNodal) =================
+            // ================= matter update (Eq. implicitFluidNodal), FP64 =================
             if (!outer_exit) {
-                double v[2] = {W3q * M[0], gs * W2q * M[0]};
-                block_sum<2>(v, red, nd->blk_out);
+                double v[2] = {W3q * (double)M[0], gs * W2q * (double)M[0]};
+                block_sum<2, double>(v, red, nd->blk_out);
                 if (tid == 0) {
                     const double rho = nd->rho;
                     const double qv0 = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * kMeVErg / rho;
@@ -569,7 +706,8 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
                     if (!stop && k >= P.max_outer) { nd->status |= NMC_NOT_CONVERGED_OUTER; stop = 1; }
                     if (!stop) {   // an iterate outside the EoS domain stops the node
                         bool ok;
-                        const double Tn = eos_temperature(rho, yn0, yn1, nd->T, &ok);
+                        const double Tn = kMixed ? eos_temperature_mixed(rho, yn0, yn1, nd->T, &ok)
+                                                 : eos_temperature(rho, yn0, yn1, nd->T, &ok);
                         if (ok) nd->T = Tn;
                         else { nd->status |= NMC_EOS_FAIL; stop = 1; }
                     }
@@ -584,9 +722,9 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
             }
         }
         // ================= finalize =================
-        {   // q(M, y) at the final moments (Eq. implicitFluidNodal)
-            double v[2] = {W3q * M[0], gs * W2q * M[0]};
-            block_sum<2>(v, red, nd->blk_out);
+        {   // q(M, y) at the final moments (Eq. implicitFluidNodal), FP64
+            double v[2] = {W3q * (double)M[0], gs * W2q * (double)M[0]};
+            block_sum<2, double>(v, red, nd->blk_out);
             if (tid == 0) {
                 nd->qv[0] = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * kMeVErg / nd->rho;
                 nd->qv[1] = nd->ystar[1] - kMB * (nd->blk_out[1] - nd->EN_star[1]) / nd->rho;
@@ -603,7 +741,8 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
                 if (P.final_q) { yo0 = nd->qv[0]; yo1 = nd->qv[1]; }   // y = q(M, y) at converged M
                 else { yo0 = nd->y[0]; yo1 = nd->y[1]; }                // Anderson-mixed iterate
                 bool ok;
-                To = eos_temperature(rho, yo0, yo1, nd->T, &ok);
+                To = kMixed ? eos_temperature_mixed(rho, yo0, yo1, nd->T, &ok)
+                            : eos_temperature(rho, yo0, yo1, nd->T, &ok);
                 if (!ok) { nd->status |= NMC_EOS_FAIL; To = nd->T; }   // last T inside the domain
             }
             a.Ye_out[n] = yo1;
@@ -615,47 +754,51 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_fp64_kernel(const SolveArgs 
         }
         if (act) {
             const long long o = (n * NS + s) * NE + q;
-            a.J_out[o] = M[0];
-            a.H_out[o * 3 + 0] = M[1];
-            a.H_out[o * 3 + 1] = M[2];
-            a.H_out[o * 3 + 2] = M[3];
+            a.J_out[o] = (double)M[0];
+            a.H_out[o * 3 + 0] = (double)M[1];
+            a.H_out[o * 3 + 1] = (double)M[2];
+            a.H_out[o * 3 + 2] = (double)M[3];
         }
         __syncthreads();
     }
 }
 
-size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, SolveArgs* a) {
+static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, bool mixed, SolveArgs* a) {
     const int NS = ctx->ns, NE = ctx->ne, NEP = ctx->nep, LD = NE + 1;
+    const size_t rs = mixed ? sizeof(float) : sizeof(double);
     const int threads = ((NS * NEP + 31) / 32) * 32;
     size_t mats = (size_t)(NS + NS / 2) * NE * LD;
-    const size_t fdq = (size_t)NS * ctx->n_elem * kProjQuad;
+    const size_t fdq = (size_t)(mixed ? 2 : 1) * NS * ctx->n_elem * kProjQuad;
     if (fdq > mats) mats = fdq;
-    const size_t vec = (size_t)6 * NS * NEP;
-    const size_t redn = (size_t)(threads / 32) * 8;
-    const size_t node = (maxm <= 3 ? sizeof(NodeShared<3>) : sizeof(NodeShared<5>)) / sizeof(double) + 1;
+    const size_t b_mats = align16(mats * rs);
+    const size_t b_vec = align16((size_t)7 * NS * NEP * rs);
+    const size_t b_red = align16((size_t)(threads / 32) * 8 * sizeof(double));
+    const size_t b_node = align16(maxm <= 3 ? sizeof(NodeShared<3>) : sizeof(NodeShared<5>));
     if (a) {
         a->off_phi = 0;
-        a->off_ann = NS * NE * LD;
-        a->off_vec = (int)mats;
-        a->off_red = (int)(mats + vec);
-        a->off_node = (int)(mats + vec + redn);
+        a->off_ann = (int)((size_t)NS * NE * LD * rs);
+        a->off_vec = (int)b_mats;
+        a->off_red = (int)(b_mats + b_vec);
+        a->off_node = (int)(b_mats + b_vec + b_red);
     }
-    return (mats + vec + redn + node) * sizeof(double);
+    return b_mats + b_vec + b_red + b_node;
 }
 
-template <int MAXM, int MAXT, int MINB>
+template <typename R, int MAXM, int MAXT, int MINB>
 static int launch_impl(nmc_ctx* ctx, SolveArgs a, cudaStream_t stream) {
-    auto kern = fused_fp64_kernel<MAXM, MAXT, MINB>;
-    const size_t smem = fused_smem_bytes(ctx, MAXM, &a);
+    auto kern = fused_kernel<R, MAXM, MAXT, MINB>;
+    const size_t smem = fused_smem_bytes(ctx, MAXM, sizeof(R) == 4, &a);
     if ((int)smem > ctx->max_smem_optin)
-        return set_error(ctx, NMC_EUNSUPPORTED, "shared-memory footprint of the fused FP64 kernel exceeds the per-block limit");
+        return set_error(ctx, NMC_EUNSUPPORTED, "shared-memory footprint of the fused kernel exceeds the per-block limit");
     const int threads = ((ctx->ns * ctx->nep + 31) / 32) * 32;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return set_error(ctx, NMC_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess || per_sm < 1)
-        return set_error(ctx, NMC_EUNSUPPORTED, "fused FP64 kernel cannot be resident with this shape");
+        return set_error(ctx, NMC_EUNSUPPORTED, "fused kernel cannot be resident with this shape");
     long long grid = (long long)per_sm * ctx->num_sms;
     if (grid > a.n) grid = a.n;
     e = cudaMemsetAsync(a.queue, 0, sizeof(int), stream);
@@ -666,17 +809,19 @@ static int launch_impl(nmc_ctx* ctx, SolveArgs a, cudaStream_t stream) {
     return NMC_OK;
 }
 
-template <int MAXM>
+template <typename R, int MAXM>
 static int launch_by_size(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream) {
     const int threads = ((ctx->ns * ctx->nep + 31) / 32) * 32;
-    if (threads <= 128) return launch_impl<MAXM, 128, 4>(ctx, a, stream);
-    if (threads <= 256) return launch_impl<MAXM, 256, 2>(ctx, a, stream);
-    return launch_impl<MAXM, 512, 1>(ctx, a, stream);
+    if (threads <= 128) return launch_impl<R, MAXM, 128, 4>(ctx, a, stream);
+    if (threads <= 256) return launch_impl<R, MAXM, 256, 2>(ctx, a, stream);
+    return launch_impl<R, MAXM, 512, 1>(ctx, a, stream);
 }
 
-int launch_fused_fp64(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream) {
-    if (a.p.m_inner <= 3) return launch_by_size<3>(ctx, a, stream);
-    return launch_by_size<5>(ctx, a, stream);
+int launch_fused(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream) {
+    const bool mixed = a.p.precision == NMC_MIXED;
+    if (a.p.m_inner <= 3)
+        return mixed ? launch_by_size<float, 3>(ctx, a, stream) : launch_by_size<double, 3>(ctx, a, stream);
+    return mixed ? launch_by_size<float, 5>(ctx, a, stream) : launch_by_size<double, 5>(ctx, a, stream);
 }
 
 }  // namespace nmc

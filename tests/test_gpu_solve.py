@@ -86,10 +86,13 @@ def test_anderson_memory_variants(case2, m_inner, m_outer):
     edges, g, tables, inp, ctx = case2
     kw = dict(TIGHT, m_inner=m_inner, m_outer=m_outer, max_inner=2000, max_outer=500)
     out = gpu_solve(ctx, inp, **kw)
-    nodes = [0, 5, 11]
+    # below 5e12 g/cm^3 every memory converges at tol 1e-13; in the dense core a
+    # short memory can stall at the cap on both sides, and capped states differ
+    nodes = [int(n) for n in np.nonzero(inp["rho"] < 5e12)[0][:3]]
     ref = _oracle(g, tables, inp, nodes, M_inner=m_inner, M_outer=m_outer, tol_inner=1e-13,
                   tol_outer=1e-13, max_inner=2000, max_outer=500)
     for n, r in zip(nodes, ref):
+        assert r["status"] == 0
         compare_node(out, n, r, g.W2, PARITY)
 
 
