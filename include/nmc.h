@@ -197,6 +197,32 @@ int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n,
                     void* stream);
 
 /*
+ * collision_solve without device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory when
+ * they solve, for example a simulation framework that reserves the GPU's
+ * memory for its own pool after set-up.  It runs the same fused kernel as
+ * collision_solve (NMC_MODE_FUSED only; same arguments, same results) but
+ * takes the kernel's only scratch, its work-queue counter, from a static
+ * 256-byte device array instead of context memory, and calls no allocation
+ * routine.  Limits and behaviour:
+ * - n <= 2^30 per call (the counter is 32-bit); larger n returns
+ *   NMC_EUNSUPPORTED with a message.
+ * - The first call on a device looks up the array's device address with that
+ *   device current; make that first call before any stream capture.
+ * - Every call on a device shares the array, and each call clears the counter
+ *   on its stream before the kernel starts: calls that overlap on the GPU
+ *   (different streams, or concurrent host threads) race and must not be
+ *   issued.
+ */
+int collision_solve_noalloc(nmc_ctx* ctx, const nmc_params* params, int64_t n,
+                            const double* rho, const double* T_in, const double* Ye_in,
+                            const double* J_in, const double* H_in, const double* dt,
+                            const double* opac_scale,
+                            double* J_out, double* H_out, double* Ye_out, double* eps_out,
+                            double* T_out, int32_t* n_outer, int32_t* n_inner, uint32_t* status,
+                            void* stream);
+
+/*
  * Tetralinear table interpolation (Sec. 2.3): value of chi_EmAb (which = 0) or
  * sigma_Iso (which = 1) of `species` at p points (rho, T, Ye, E), linear in
  * (log10 rho, log10 T, Ye, ln E) on the table's ln values, exponentiated.

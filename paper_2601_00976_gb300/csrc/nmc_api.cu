@@ -342,7 +342,7 @@ int nmc_energy_nodes(const nmc_ctx* ctx, double* eps, double* w2, double* w3, in
     return NMC_OK;
 }
 
-static int check_params(nmc_ctx* ctx, const nmc_params* p) {
+int nmc_check_params_internal(nmc_ctx* ctx, const nmc_params* p) {
     if (!p) return set_error(ctx, NMC_EINVAL, "params is NULL");
     if (!(p->tol_inner > 0.0) || !(p->tol_outer > 0.0) || !std::isfinite(p->tol_inner) || !std::isfinite(p->tol_outer))
         return set_error(ctx, NMC_EINVAL, "tolerances must be positive and finite");
@@ -364,7 +364,7 @@ int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n, const dou
                     double* Ye_out, double* eps_out, double* T_out, int32_t* n_outer,
                     int32_t* n_inner, uint32_t* status, void* stream) {
     if (!ctx) return NMC_EINVAL;
-    int rc = check_params(ctx, params);
+    int rc = nmc_check_params_internal(ctx, params);
     if (rc != NMC_OK) return rc;
     if (n < 0) return set_error(ctx, NMC_EINVAL, "n < 0");
     if (n > (int64_t(1) << 30)) return set_error(ctx, NMC_EUNSUPPORTED, "n > 2^30 nodes per call");

@@ -121,3 +121,5 @@ int launch_opacity_interp(nmc_ctx* ctx, int which, int species, long long p, con
 size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, bool mixed, SolveArgs* a);
 int set_error(nmc_ctx* ctx, int code, const std::string& msg);
 }  // namespace nmc
+
+extern "C" int nmc_check_params_internal(nmc_ctx* ctx, const nmc_params* p);

@@ -53,7 +53,8 @@ class Params(ctypes.Structure):
 
 
 EXPORTS = ("nmc_default_params", "nmc_create", "nmc_destroy", "nmc_last_error", "nmc_energy_nodes",
-           "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "opacity_interp")
+           "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "collision_solve_noalloc",
+           "opacity_interp")
 
 _lib = None
 
@@ -83,6 +84,8 @@ def load_library(path=LIB_PATH):
     lib.nmc_geometric_edges.restype = ctypes.c_int
     lib.collision_solve.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 16
     lib.collision_solve.restype = ctypes.c_int
+    lib.collision_solve_noalloc.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 16
+    lib.collision_solve_noalloc.restype = ctypes.c_int
     lib.opacity_interp.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64] + [vp] * 6
     lib.opacity_interp.restype = ctypes.c_int
     _lib = lib
