@@ -1,23 +1,38 @@
 """Gradient of a converged collision solve by the implicit-function theorem (oracle).
 
-At v = 0 with y returned as q(M, y) at the converged moments, the outputs
-(D, Ye, eps) of Algorithm 1 are fixed by the reduced system
+Test infrastructure: only the tests and the benchmark's CPU baseline use it.
+
+At v = 0, with y returned as q(M, y) at the converged moments, the outputs of
+Algorithm 1 are fixed by the reduced system
 
     G(D; p) = D - Q_D(D, q(D; p); p) = 0                                (*)
 
 (the number part of Eq. implicitMomentsNodal with y eliminated through
-Eq. implicitFluidNodal; Q_D does not depend on I at v = 0), with
-Ye = q_Ye(D; p), eps = q_eps(D; p).  p collects the step's inputs: the old
-moments D*, the old state (Ye*, T*) and the four opacity scale factors.  For a
-loss L = gD . D + gYe Ye + geps eps the IFT gives
+Eq. implicitFluidNodal; Q_D does not depend on I at v = 0).  The other outputs
+are explicit functions of the root D:
+  - Ye = q_Ye(D; p) and eps = q_eps(D; p), the matter update;
+  - T = T(eps, Ye) by the EoS;
+  - H = I* / (1 + dtau kappa(D, y)), the first-moment part of
+    Eq. implicitMomentsNodal at v = 0.
+p collects the step's inputs: the old moments (D*, I*), the old matter state
+(Ye*, T*) and the four opacity scale factors.  With frozen matter, y = y* and
+q is the identity on y*.
 
-    lambda = (dG/dD)^-T (gD + gYe dYe/dD + geps deps/dD)
-    dL/dp  = -lambda . dG/dp + gYe dYe/dp + geps deps/dp.
+For a loss L = gD . D + gYe Ye + geps eps + gT T + gH . H, write
+L_x(D; p) for its value at given D.  The IFT gives
 
-Every Jacobian here is formed by central finite differences of the oracle's
-own residual functions, so this gradient shares no derivative formula with the
-CUDA adjoint.  The old first moments I* do not enter (*) or the outputs at
-v = 0, so their gradient is zero.
+    lambda = (dG/dD)^-T dL_x/dD,       dL/dp = dL_x/dp - lambda . dG/dp.
+
+Every derivative here is a central finite difference of the oracle's own
+functions, so this gradient shares no derivative formula with the CUDA
+adjoint.  Differences use the fourth-order central stencil
+f' = (8 (f(h) - f(-h)) - (f(2h) - f(-2h))) / (12 h).  Steps in D and D* are
+rel times the entry's natural scale s_j: the change of D_j that moves the
+matter state by O(1) relative, s_j = min(1, rho eps / (MeV W3_j),
+rho Ye / (m_B |g_s| W2_j)) (1 with frozen matter).  The map is smooth on that
+scale (its terms D (1 - D), 1 + dtau chi(D) and the matter update), whereas a
+step relative to an entry of 1e-30 would leave only rounding, and a step of
+1e-6 in a bin of large W3 would move T far enough for curvature to show.
 """
 
 import numpy as np
@@ -28,89 +43,126 @@ from .opacities import compute_opacities
 from .solver import moment_map, matter_map, neutrino_energy_number
 
 
-def _parts(grid, tables, params, rho, p, D):
-    """(G(D; p), Ye(D; p), eps(D; p)) for parameters p = (D*, Ye*, T*, scale, dt)."""
-    D_star, Ye_star, T_star, scale, dt = p
-    ns, ne = D_star.shape
+def _matter(grid, tables, params, rho, p, D):
+    """Matter state y = q(D; p) (or y* with frozen matter), its T and the opacities there."""
+    D_star, _, Ye_star, T_star, scale, dt = p
+    ns = D_star.shape[0]
     g = lepton_numbers(ns)
     eps_star = eos.specific_energy(rho, T_star, Ye_star)
     y_star = np.array([eps_star, Ye_star])
-    EN_star = neutrino_energy_number(D_star, grid, g)
-    y = matter_map(D, rho, y_star, EN_star, grid, g)
+    if params.frozen_matter:
+        y = y_star
+    else:
+        EN_star = neutrino_energy_number(D_star, grid, g)
+        y = matter_map(D, rho, y_star, EN_star, grid, g)
     T, _ = eos.temperature(rho, y[0], y[1])
     op = compute_opacities(grid, tables, rho, T, y[1], scale, params.proc_mask, params.dmin, params.dmax)
+    return y, T, op
+
+
+def _outputs(grid, tables, params, rho, p, D, state=None):
+    """(G, Ye, eps, T, H) at moments D for parameters p = (D*, I*, Ye*, T*, scale, dt)."""
+    D_star, I_star, _, _, _, dt = p
+    y, T, op = state if state is not None else _matter(grid, tables, params, rho, p, D)
+    ns, ne = D_star.shape
     M = np.zeros((ns, ne, 4))
     M[:, :, 0] = D
     Ms = np.zeros((ns, ne, 4))
     Ms[:, :, 0] = D_star
+    Ms[:, :, 1:] = I_star
     Q = moment_map(M, Ms, op, grid.W2, C_LIGHT * dt)
-    return D - Q[:, :, 0], y[1], y[0]
+    return D - Q[:, :, 0], y[1], y[0], T, Q[:, :, 1:]
 
 
-def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, dt, scale, D, gD, gYe, geps, rel=1e-6):
+def _stencil(f, h):
+    """Fourth-order central difference of the vector function f(t) at t = 0."""
+    return (8.0 * (f(h) - f(-h)) - (f(2.0 * h) - f(-2.0 * h))) / (12.0 * h)
+
+
+def natural_scale(grid, params, rho, eps, Ye, ns):
+    """s[s, q]: the change of D_sq that moves (eps, Ye) by O(1) relative."""
+    from .constants import MEV_TO_ERG, M_B
+    s = np.ones((ns, grid.ne))
+    if params.frozen_matter:
+        return s
+    g = np.asarray(lepton_numbers(ns), dtype=float)
+    s = np.minimum(s, (rho * abs(eps) / (MEV_TO_ERG * grid.W3))[None, :])
+    with np.errstate(divide="ignore"):
+        sy = rho * abs(Ye) / (M_B * np.abs(g)[:, None] * grid.W2[None, :])
+    return np.minimum(s, sy)
+
+
+def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, scale, D,
+             gD=None, gYe=0.0, geps=0.0, gT=0.0, gH=None, rel=1e-5):
     """dL/d(D*, I*, Ye*, T*, scale) at the converged moments D of one node.
 
     Returns a dict with keys D_star (ns, ne), I_star (ns, ne, 3), Ye, T, scale (4,).
     """
     ns, ne = D.shape
     n = ns * ne
-    p0 = (np.array(D_star, dtype=float), float(Ye_star), float(T_star), np.array(scale, dtype=float), float(dt))
+    gD = np.zeros((ns, ne)) if gD is None else np.asarray(gD, dtype=float)
+    gH = np.zeros((ns, ne, 3)) if gH is None else np.asarray(gH, dtype=float)
+    p0 = (np.array(D_star, dtype=float), np.array(I_star, dtype=float), float(Ye_star), float(T_star),
+          np.array(scale, dtype=float), float(dt))
+    D = np.asarray(D, dtype=float)
 
-    def G_of_D(Dv):
-        return _parts(grid, tables, params, rho, p0, Dv.reshape(ns, ne))
+    def vec(p, Dm, state=None):
+        """(G, L_x) at moments Dm for parameters p, as one vector."""
+        G, Ye, eps, T, H = _outputs(grid, tables, params, rho, p, Dm, state)
+        Lx = float(np.sum(gD * Dm) + gYe * Ye + geps * eps + gT * T + np.sum(gH * H))
+        return np.concatenate([G.ravel(), [Lx]])
 
-    # dG/dD and dYe/dD, deps/dD by central differences
+    y, _, _ = _matter(grid, tables, params, rho, p0, D)
+    sD = natural_scale(grid, params, rho, y[0], y[1], ns).ravel()
+    # dG/dD and dL_x/dD
     J = np.empty((n, n))
-    dYe = np.empty(n)
-    deps = np.empty(n)
-    Dv = D.ravel().astype(float)
+    dLx = np.empty(n)
+    Dv = D.ravel()
     for j in range(n):
-        h = rel * max(abs(Dv[j]), 1e-8)
-        up, dn = Dv.copy(), Dv.copy()
-        up[j] += h
-        dn[j] -= h
-        Gu, Yu, Eu = G_of_D(up)
-        Gd, Yd, Ed = G_of_D(dn)
-        J[:, j] = (Gu - Gd).ravel() / (2 * h)
-        dYe[j] = (Yu - Yd) / (2 * h)
-        deps[j] = (Eu - Ed) / (2 * h)
-    rhs = np.asarray(gD, dtype=float).ravel() + gYe * dYe + geps * deps
-    lam = np.linalg.solve(J.T, rhs)
+        def f(t, j=j):
+            Dp = Dv.copy()
+            Dp[j] += t
+            return vec(p0, Dp.reshape(ns, ne))
+        d = _stencil(f, rel * sD[j])
+        J[:, j] = d[:-1]
+        dLx[j] = d[-1]
+    lam = np.linalg.solve(J.T, dLx)
 
-    def dL_dp(perturb):
-        """-lambda . dG/dp + gYe dYe/dp + geps deps/dp for one scalar parameter."""
-        (pu, hu), (pd, hd) = perturb(+1), perturb(-1)
-        Gu, Yu, Eu = _parts(grid, tables, params, rho, pu, D)
-        Gd, Yd, Ed = _parts(grid, tables, params, rho, pd, D)
-        h = hu - hd
-        return (-lam @ (Gu - Gd).ravel() + gYe * (Yu - Yd) + geps * (Eu - Ed)) / h
+    def dL_dp(make, h, state=None):
+        """dL_x/dp - lambda . dG/dp for one scalar parameter; make(t) returns p with that parameter + t."""
+        d = _stencil(lambda t: vec(make(t), D, state), h)
+        return d[-1] - lam @ d[:-1]
 
+    def set_entry(idx, index):
+        def make(t):
+            lst = list(p0)
+            if index is None:
+                lst[idx] = lst[idx] + t
+            else:
+                a = lst[idx].copy()
+                a[index] += t
+                lst[idx] = a
+            return tuple(lst)
+        return make
+
+    ys = (eos.specific_energy(rho, p0[3], p0[2]), p0[2])
+    sDs = natural_scale(grid, params, rho, ys[0], ys[1], ns)
     out_D = np.empty((ns, ne))
     for s in range(ns):
         for q in range(ne):
-            def pert(sign, s=s, q=q):
-                Ds = p0[0].copy()
-                h = rel * max(abs(Ds[s, q]), 1e-8)
-                Ds[s, q] += sign * h
-                return (Ds,) + p0[1:], sign * h
-            out_D[s, q] = dL_dp(pert)
-
-    def pert_scalar(idx):
-        def pert(sign):
-            lst = list(p0)
-            h = rel * abs(lst[idx])
-            lst[idx] = lst[idx] + sign * h
-            return tuple(lst), sign * h
-        return pert
-
-    g_Ye = dL_dp(pert_scalar(1))
-    g_T = dL_dp(pert_scalar(2))
+            out_D[s, q] = dL_dp(set_entry(0, (s, q)), rel * sDs[s, q])
+    # I* enters neither q nor the opacities: the matter state at D is shared by its perturbations,
+    # and G and the outputs are linear in I*
+    state = _matter(grid, tables, params, rho, p0, D)
+    hI = rel * max(np.max(np.abs(p0[1])), 1e-300)
+    out_I = np.empty((ns, ne, 3))
+    for s in range(ns):
+        for q in range(ne):
+            for c in range(3):
+                out_I[s, q, c] = dL_dp(set_entry(1, (s, q, c)), hI, state)
+    g_Ye = dL_dp(set_entry(2, None), rel * abs(p0[2]))
+    g_T = dL_dp(set_entry(3, None), rel * abs(p0[3]))
     g_scale = np.empty(4)
     for k in range(4):
-        def pert(sign, k=k):
-            sc = p0[3].copy()
-            h = rel * max(abs(sc[k]), 1e-3)
-            sc[k] += sign * h
-            return (p0[0], p0[1], p0[2], sc, p0[4]), sign * h
-        g_scale[k] = dL_dp(pert)
-    return dict(D_star=out_D, I_star=np.zeros((ns, ne, 3)), Ye=g_Ye, T=g_T, scale=g_scale)
+        g_scale[k] = dL_dp(set_entry(4, k), rel * max(abs(p0[4][k]), 1e-3))
+    return dict(D_star=out_D, I_star=out_I, Ye=g_Ye, T=g_T, scale=g_scale)

@@ -1,66 +1,94 @@
 """Pin of the oracle's IFT gradient: central finite differences of full solves.
 
-The gradient of L = gD . D_out + gYe Ye_out + geps eps_out with respect to the
-step's inputs, from the implicit-function theorem on the converged solve, must
-match central differences (h = 1e-6 relative) of Algorithm 1 itself, run to
-tol 1e-14 so that the solver tolerance does not swamp the difference quotient.
+The gradient of L = gD . D_out + gYe Ye_out + geps eps_out + gT T_out + gH . H_out
+with respect to the step's inputs, from the implicit-function theorem on the
+converged solve, must match fourth-order central differences (h = 1e-5 relative) of
+Algorithm 1 itself, run to tol 1e-14 so that the solver tolerance does not
+swamp the difference quotient.  Coupled and frozen matter are both checked.
 """
 
 import numpy as np
 import pytest
 
-from oracle import solver, adjoint
+from oracle import solver, adjoint, eos
 from paper_2601_00976_gb300 import synthetic
 
-TIGHT = solver.Params(tol_inner=1e-14, tol_outer=1e-14, max_inner=3000, max_outer=300)
+TIGHT = dict(tol_inner=1e-14, tol_outer=1e-14, max_inner=3000, max_outer=300)
 
 
-def _loss(g, t, n, inp, gD, gYe, geps, D_star=None, Ye=None, T=None, scale=None):
-    r = solver.solve_node(g, t, TIGHT, inp["rho"][n], inp["T"][n] if T is None else T,
-                          inp["Ye"][n] if Ye is None else Ye,
-                          inp["D"][n] if D_star is None else D_star, inp["I"][n], inp["dt"][n],
-                          inp["scale"][n] if scale is None else scale)
-    assert r["status"] == 0
-    return float(np.sum(gD * r["D"]) + gYe * r["Ye"] + geps * r["eps"]), r
+class _Case:
+    def __init__(self, grid, n, frozen, seed):
+        self.g = grid
+        self.params = solver.Params(frozen_matter=frozen, **TIGHT)
+        self.t = synthetic.make_tables(grid.eps, 2, seed=6)
+        self.inp = synthetic.make_inputs("profile", 2, grid.eps, 2, seed=40)
+        self.n = n
+        rng = np.random.default_rng(seed)
+        ne = grid.ne
+        self.gD = rng.normal(size=(2, ne))
+        self.gYe = rng.normal()
+        self.geps = rng.normal() * 1e-18
+        self.gT = rng.normal()
+        self.gH = rng.normal(size=(2, ne, 3))
+
+    def loss(self, **over):
+        i, n = self.inp, self.n
+        args = dict(rho=i["rho"][n], T=i["T"][n], Ye=i["Ye"][n], D=i["D"][n], I=i["I"][n], scale=i["scale"][n])
+        args.update(over)
+        r = solver.solve_node(self.g, self.t, self.params, args["rho"], args["T"], args["Ye"], args["D"],
+                              args["I"], i["dt"][n], args["scale"])
+        assert r["status"] == 0
+        L = (np.sum(self.gD * r["D"]) + self.gYe * r["Ye"] + self.geps * r["eps"] + self.gT * r["T"]
+             + np.sum(self.gH * r["I"]))
+        return float(L), r
 
 
-@pytest.mark.parametrize("n", [0, 1])
-def test_ift_gradient_matches_finite_differences(grid_tiny, n):
-    g = grid_tiny
-    t = synthetic.make_tables(g.eps, 2, seed=6)
-    inp = synthetic.make_inputs("profile", 2, g.eps, 2, seed=40)
-    rng = np.random.default_rng(41 + n)
-    gD = rng.normal(size=(2, g.ne))
-    gYe, geps = rng.normal(), rng.normal() / inp["T"][n] * 1e-18
-    L0, r = _loss(g, t, n, inp, gD, gYe, geps)
-    grad = adjoint.gradient(g, t, TIGHT, inp["rho"][n], inp["T"][n], inp["Ye"][n], inp["D"][n], inp["dt"][n],
-                            inp["scale"][n], r["D"], gD, gYe, geps)
-    fd = {}
-    h = 1e-6
-    for key, base in (("Ye", inp["Ye"][n]), ("T", inp["T"][n])):
-        Lu, _ = _loss(g, t, n, inp, gD, gYe, geps, **{key: base * (1 + h)})
-        Ld, _ = _loss(g, t, n, inp, gD, gYe, geps, **{key: base * (1 - h)})
-        fd[key] = (Lu - Ld) / (2 * h * base)
-    fd_scale = np.empty(4)
-    for k in range(4):
-        su, sd = inp["scale"][n].copy(), inp["scale"][n].copy()
-        su[k] *= 1 + h
-        sd[k] *= 1 - h
-        fd_scale[k] = (_loss(g, t, n, inp, gD, gYe, geps, scale=su)[0]
-                       - _loss(g, t, n, inp, gD, gYe, geps, scale=sd)[0]) / (2 * h * inp["scale"][n][k])
-    fd_D = {}
-    for (s, q) in [(0, 0), (0, 5), (1, 3), (1, 7)]:
-        Du, Dd = inp["D"][n].copy(), inp["D"][n].copy()
-        dh = h * max(abs(Du[s, q]), 1e-8)
-        Du[s, q] += dh
-        Dd[s, q] -= dh
-        fd_D[(s, q)] = (_loss(g, t, n, inp, gD, gYe, geps, D_star=Du)[0]
-                        - _loss(g, t, n, inp, gD, gYe, geps, D_star=Dd)[0]) / (2 * dh)
-    assert grad["Ye"] == pytest.approx(fd["Ye"], rel=1e-6, abs=1e-9 * abs(fd["Ye"]) + 1e-12)
-    assert grad["T"] == pytest.approx(fd["T"], rel=1e-6)
-    scale_ref = np.max(np.abs(fd_scale))
-    assert np.max(np.abs(grad["scale"] - fd_scale)) <= 1e-6 * scale_ref, (grad["scale"], fd_scale)
-    d_ref = np.max(np.abs(list(fd_D.values())))
-    for (s, q), v in fd_D.items():
-        assert abs(grad["D_star"][s, q] - v) <= 1e-6 * d_ref, ((s, q), grad["D_star"][s, q], v)
+@pytest.mark.parametrize("n,frozen", [(0, 0), (1, 0), (1, 1)])
+def test_ift_gradient_matches_finite_differences(grid_tiny, n, frozen):
+    c = _Case(grid_tiny, n, frozen, seed=41 + n + 7 * frozen)
+    i = c.inp
+    _, r = c.loss()
+    grad = adjoint.gradient(c.g, c.t, c.params, i["rho"][n], i["T"][n], i["Ye"][n], i["D"][n], i["I"][n],
+                            i["dt"][n], i["scale"][n], r["D"], gD=c.gD, gYe=c.gYe, geps=c.geps, gT=c.gT, gH=c.gH)
+    h = 1e-5
+    # fourth-order central differences of full solves; steps in D* scaled per entry by the change that
+    # moves the matter state by O(1) relative (the solve is smooth on that scale)
+    eps_star = eos.specific_energy(i["rho"][n], i["T"][n], i["Ye"][n])
+    sD = adjoint.natural_scale(c.g, c.params, i["rho"][n], eps_star, i["Ye"][n], 2)
+
+    def central(key, base, idx=None, step=None):
+        def L(t):
+            if idx is None:
+                return c.loss(**{key: base + t})[0]
+            v = base.copy()
+            v[idx] += t
+            return c.loss(**{key: v})[0]
+        d = step if step is not None else h * abs(base if idx is None else base[idx])
+        return (8 * (L(d) - L(-d)) - (L(2 * d) - L(-2 * d))) / (12 * d)
+
+    fd_Ye = central("Ye", i["Ye"][n])
+    fd_T = central("T", i["T"][n])
+    assert grad["Ye"] == pytest.approx(fd_Ye, rel=1e-6, abs=1e-6 * abs(fd_T) * i["T"][n] / i["Ye"][n])
+    assert grad["T"] == pytest.approx(fd_T, rel=1e-6)
+    fd_scale = np.array([central("scale", i["scale"][n], k, h * max(i["scale"][n][k], 1e-3)) for k in range(4)])
+    assert np.max(np.abs(grad["scale"] - fd_scale)) <= 1e-6 * np.max(np.abs(fd_scale)), (grad["scale"], fd_scale)
+    fd_D = {sq: central("D", i["D"][n], sq, h * sD[sq]) for sq in [(0, 0), (0, 5), (1, 3), (1, 7)]}
+    d_ref = max(abs(v) for v in fd_D.values())
+    for sq, v in fd_D.items():
+        assert abs(grad["D_star"][sq] - v) <= 1e-6 * abs(v) + 1e-9 * d_ref, (sq, grad["D_star"][sq], v)
+    hI = h * np.max(np.abs(i["I"][n]))
+    fd_I = {sqc: central("I", i["I"][n], sqc, hI) for sqc in [(0, 1, 0), (0, 6, 2), (1, 2, 1), (1, 7, 0)]}
+    i_ref = max(abs(v) for v in fd_I.values())
+    for sqc, v in fd_I.items():
+        assert abs(grad["I_star"][sqc] - v) <= 1e-6 * abs(v) + 1e-9 * i_ref, (sqc, grad["I_star"][sqc], v)
+
+
+def test_gradient_without_first_moment_cotangent_ignores_I_star(grid_tiny):
+    """With gH = 0 the outputs that remain do not depend on I* at v = 0."""
+    c = _Case(grid_tiny, 0, 0, seed=3)
+    i = c.inp
+    _, r = c.loss()
+    grad = adjoint.gradient(c.g, c.t, c.params, i["rho"][0], i["T"][0], i["Ye"][0], i["D"][0], i["I"][0],
+                            i["dt"][0], i["scale"][0], r["D"], gD=c.gD, gYe=c.gYe, geps=c.geps)
     assert np.all(grad["I_star"] == 0.0)
+    assert grad["scale"][1] == 0.0   # isoenergetic scattering enters only H
