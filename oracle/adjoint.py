@@ -19,9 +19,14 @@ p collects the step's inputs: the old moments (D*, I*), the old matter state
 q is the identity on y*.
 
 For a loss L = gD . D + gYe Ye + geps eps + gT T + gH . H, write
-L_x(D; p) for its value at given D.  The IFT gives
+L_x(D; p) for its value at given D and O = (Ye, eps, T, H) for the explicit
+outputs, g_O for their cotangents.  The IFT gives
 
-    lambda = (dG/dD)^-T dL_x/dD,       dL/dp = dL_x/dp - lambda . dG/dp.
+    lambda = (dG/dD)^-T dL_x/dD,       dL/dp = dL_x/dp - lambda . dG/dp,
+
+with dL_x/dD = gD + g_O . dO/dD and dL_x/dp = g_O . dO/dp.  G and O are
+differenced as vectors and contracted afterwards, so each quotient's rounding
+is relative to its own output rather than to the whole loss.
 
 Every derivative here is a central finite difference of the oracle's own
 functions, so this gradient shares no derivative formula with the CUDA
@@ -106,11 +111,12 @@ def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, sca
           np.array(scale, dtype=float), float(dt))
     D = np.asarray(D, dtype=float)
 
+    gO = np.concatenate([[gYe, geps, gT], gH.ravel()])
+
     def vec(p, Dm, state=None):
-        """(G, L_x) at moments Dm for parameters p, as one vector."""
+        """(G, O) at moments Dm for parameters p, as one vector."""
         G, Ye, eps, T, H = _outputs(grid, tables, params, rho, p, Dm, state)
-        Lx = float(np.sum(gD * Dm) + gYe * Ye + geps * eps + gT * T + np.sum(gH * H))
-        return np.concatenate([G.ravel(), [Lx]])
+        return np.concatenate([G.ravel(), [Ye, eps, T], H.ravel()])
 
     y, _, _ = _matter(grid, tables, params, rho, p0, D)
     sD = natural_scale(grid, params, rho, y[0], y[1], ns).ravel()
@@ -124,14 +130,14 @@ def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, sca
             Dp[j] += t
             return vec(p0, Dp.reshape(ns, ne))
         d = _stencil(f, rel * sD[j])
-        J[:, j] = d[:-1]
-        dLx[j] = d[-1]
+        J[:, j] = d[:n]
+        dLx[j] = gD.ravel()[j] + gO @ d[n:]
     lam = np.linalg.solve(J.T, dLx)
 
     def dL_dp(make, h, state=None):
         """dL_x/dp - lambda . dG/dp for one scalar parameter; make(t) returns p with that parameter + t."""
         d = _stencil(lambda t: vec(make(t), D, state), h)
-        return d[-1] - lam @ d[:-1]
+        return gO @ d[n:] - lam @ d[:n]
 
     def set_entry(idx, index):
         def make(t):
