@@ -31,13 +31,16 @@ is relative to its own output rather than to the whole loss.
 Every derivative here is a central finite difference of the oracle's own
 functions, so this gradient shares no derivative formula with the CUDA
 adjoint.  Differences use the fourth-order central stencil
-f' = (8 (f(h) - f(-h)) - (f(2h) - f(-2h))) / (12 h).  Steps in D and D* are
-rel times the entry's natural scale s_j: the change of D_j that moves the
+f' = (8 (f(h) - f(-h)) - (f(2h) - f(-2h))) / (12 h).  Steps in D and D* start
+at rel times the entry's natural scale s_j: the change of D_j that moves the
 matter state by O(1) relative, s_j = min(1, rho eps / (MeV W3_j),
-rho Ye / (m_B |g_s| W2_j)) (1 with frozen matter).  The map is smooth on that
-scale (its terms D (1 - D), 1 + dtau chi(D) and the matter update), whereas a
-step relative to an entry of 1e-30 would leave only rounding, and a step of
-1e-6 in a bin of large W3 would move T far enough for curvature to show.
+rho Ye / (m_B |g_s| W2_j)) (1 with frozen matter); a step relative to an
+entry of 1e-30 would leave only rounding, and a step of 1e-6 in a bin of large
+W3 would move T far enough for curvature to show.  At fixed y the map is a
+ratio of functions affine in D whose denominator 1 + dtau chi can vary on a
+much smaller scale in bins where dtau K W~ is large, so these steps are then
+cut by 4 until two successive estimates agree element by element (to 1e-9
+relative, or to their rounding).
 """
 
 import numpy as np
@@ -84,6 +87,20 @@ def _stencil(f, h):
     return (8.0 * (f(h) - f(-h)) - (f(2.0 * h) - f(-2.0 * h))) / (12.0 * h)
 
 
+def _stencil_refined(f, h, mag, levels=4):
+    """_stencil with the step cut by 4 until successive estimates agree elementwise;
+    mag[i] is the size of the terms that f[i] is formed from (its rounding scale)."""
+    d = _stencil(f, h)
+    for _ in range(levels):
+        h4 = 0.25 * h
+        d2 = _stencil(f, h4)
+        noise = 64.0 * np.finfo(float).eps * mag / h4
+        if np.all(np.abs(d2 - d) <= 1e-8 * np.abs(d2) + noise):
+            return d2
+        d, h = d2, h4
+    return d
+
+
 def natural_scale(grid, params, rho, eps, Ye, ns):
     """s[s, q]: the change of D_sq that moves (eps, Ye) by O(1) relative."""
     from .constants import MEV_TO_ERG, M_B
@@ -118,8 +135,11 @@ def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, sca
         G, Ye, eps, T, H = _outputs(grid, tables, params, rho, p, Dm, state)
         return np.concatenate([G.ravel(), [Ye, eps, T], H.ravel()])
 
-    y, _, _ = _matter(grid, tables, params, rho, p0, D)
+    y, T0, _ = _matter(grid, tables, params, rho, p0, D)
     sD = natural_scale(grid, params, rho, y[0], y[1], ns).ravel()
+    # rounding scale of each entry of vec: G = D - Q_D is formed from terms of size |D|
+    H0 = _outputs(grid, tables, params, rho, p0, D)[4]
+    mag = np.concatenate([np.abs(D).ravel(), np.abs([y[1], y[0], T0]), np.abs(H0).ravel()]) + 1e-300
     # dG/dD and dL_x/dD
     J = np.empty((n, n))
     dLx = np.empty(n)
@@ -129,14 +149,15 @@ def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, sca
             Dp = Dv.copy()
             Dp[j] += t
             return vec(p0, Dp.reshape(ns, ne))
-        d = _stencil(f, rel * sD[j])
+        d = _stencil_refined(f, rel * sD[j], mag)
         J[:, j] = d[:n]
         dLx[j] = gD.ravel()[j] + gO @ d[n:]
     lam = np.linalg.solve(J.T, dLx)
 
-    def dL_dp(make, h, state=None):
+    def dL_dp(make, h, state=None, refine=False):
         """dL_x/dp - lambda . dG/dp for one scalar parameter; make(t) returns p with that parameter + t."""
-        d = _stencil(lambda t: vec(make(t), D, state), h)
+        fp = lambda t: vec(make(t), D, state)  # noqa: E731
+        d = _stencil_refined(fp, h, mag) if refine else _stencil(fp, h)
         return gO @ d[n:] - lam @ d[:n]
 
     def set_entry(idx, index):
@@ -156,7 +177,7 @@ def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, sca
     out_D = np.empty((ns, ne))
     for s in range(ns):
         for q in range(ne):
-            out_D[s, q] = dL_dp(set_entry(0, (s, q)), rel * sDs[s, q])
+            out_D[s, q] = dL_dp(set_entry(0, (s, q)), rel * sDs[s, q], refine=True)
     # I* enters neither q nor the opacities: the matter state at D is shared by its perturbations,
     # and G and the outputs are linear in I*
     state = _matter(grid, tables, params, rho, p0, D)
