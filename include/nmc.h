@@ -233,6 +233,61 @@ int opacity_interp(nmc_ctx* ctx, int32_t which, int32_t species, int64_t p,
                    const double* rho, const double* T, const double* Ye, const double* E,
                    double* out, void* stream);
 
+/*
+ * Gradient of a converged collision_solve at n nodes (FP64), by the
+ * implicit-function theorem (one transposed linear solve per node).  The
+ * paper states the implicit step (Eqs. implicitMomentsNodal,
+ * implicitFluidNodal, with Eqs. eulerianEnergyLG and eulerianNumberLG); its
+ * derivative is this library's addition.
+ *
+ * At v = 0 the solve's outputs are fixed by its number moments: D (J_out) is
+ * the root of G(D) = D - Q_D(D, q(D)) = 0 with y = q(D) the matter update,
+ * Ye_out and eps_out are q(D), T_out the EoS temperature of (eps_out, Ye_out),
+ * and H_out = I* / (1 + dtau kappa(D, y)).  Given cotangents of those outputs,
+ * the call returns the cotangents of the inputs D* (J_in), I* (H_in), Ye_in,
+ * T_in and the four opacity scale factors.  dQ_D/dD and dkappa/dD are formed
+ * analytically from the node's kernel matrices; dQ_D/dy and dkappa/dy by
+ * central differences with steps 1e-6 |eps| and 1e-6 |Ye|.  Each node's
+ * Jacobian is solved by Gaussian elimination with partial pivoting per
+ * particle/antiparticle pair plus a rank-2 (Woodbury) update for the matter
+ * coupling.  The gradient is that of the exact root, so it describes the
+ * solve up to the solve's own tolerance.  params must be those of the forward
+ * call: proc_mask, d_min, d_max and frozen_matter enter; tolerances,
+ * precision and mode do not (the adjoint always runs in FP64).
+ *
+ * Inputs (DEVICE, float64):
+ *   rho, T_in, Ye_in, J_in, dt, opac_scale   the forward call's inputs
+ *                                            (opac_scale may be NULL = ones)
+ *   H_in[n][ns][ne][3]                       I*; may be NULL when gH_out is NULL
+ *   J_out[n][ns][ne]                         converged D from the forward call
+ *   T_out[n] or NULL                         forward T_out, the starting guess
+ *                                            of the EoS solve (NULL: T_in)
+ *   gJ_out[n][ns][ne], gH_out[n][ns][ne][3], gYe_out[n], geps_out[n], gT_out[n]
+ *                                            cotangents; any may be NULL = 0
+ * Outputs (DEVICE, float64):
+ *   gJ_in[n][ns][ne], gYe_in[n], gT_in[n]    required
+ *   gH_in[n][ns][ne][3] or NULL              gH_out / (1 + dtau kappa)
+ *   gscale[n][4] or NULL                     EmAb, Iso, NES, Pair
+ *   status[n] or NULL                        NMC_BAD_INPUT, NMC_EOS_FAIL,
+ *                                            NMC_NONFINITE (singular or
+ *                                            non-finite), NMC_TABLE_CLAMP; a
+ *                                            node with any of the first three
+ *                                            gets zero gradients
+ * Outputs must not overlap inputs.  Supported shapes: those of
+ * collision_solve whose per-block shared memory (kernel matrices plus one
+ * 2ne x (2ne+3) FP64 pair system) fits in 227 KB, e.g. ne <= 32 with 4 or 6
+ * species; otherwise NMC_EUNSUPPORTED.
+ */
+int collision_adjoint(nmc_ctx* ctx, const nmc_params* params, int64_t n,
+                      const double* rho, const double* T_in, const double* Ye_in,
+                      const double* J_in, const double* H_in, const double* dt,
+                      const double* opac_scale,
+                      const double* J_out, const double* T_out,
+                      const double* gJ_out, const double* gH_out, const double* gYe_out,
+                      const double* geps_out, const double* gT_out,
+                      double* gJ_in, double* gH_in, double* gYe_in, double* gT_in,
+                      double* gscale, uint32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

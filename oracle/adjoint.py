@@ -39,8 +39,11 @@ entry of 1e-30 would leave only rounding, and a step of 1e-6 in a bin of large
 W3 would move T far enough for curvature to show.  At fixed y the map is a
 ratio of functions affine in D whose denominator 1 + dtau chi can vary on a
 much smaller scale in bins where dtau K W~ is large, so these steps are then
-cut by 4 until two successive estimates agree element by element (to 1e-9
-relative, or to their rounding).
+cut by 4 until two successive estimates agree element by element (to 1e-8
+relative, or to their rounding).  The scale factors do not move y at fixed D,
+so Q_D and H are ratios of functions affine in s_k whose nonlinearity scale is
+at least s_k: their steps start at 1e-3 s_k (refined the same way), which keeps
+the rounding of G, amplified by large entries of lambda, far below 1e-9.
 """
 
 import numpy as np
@@ -114,11 +117,55 @@ def natural_scale(grid, params, rho, eps, Ye, ns):
     return np.minimum(s, sy)
 
 
+def _vec_fn(grid, tables, params, rho):
+    def vec(p, Dm, state=None):
+        """(G, Ye, eps, T, H) at moments Dm for parameters p, as one vector."""
+        G, Ye, eps, T, H = _outputs(grid, tables, params, rho, p, Dm, state)
+        return np.concatenate([G.ravel(), [Ye, eps, T], H.ravel()])
+    return vec
+
+
+def _jacobian(grid, tables, params, rho, p0, D, rel):
+    """(dG/dD, dO/dD, rounding scale of vec's entries) at moments D, O = (Ye, eps, T, H)."""
+    ns, ne = D.shape
+    n = ns * ne
+    vec = _vec_fn(grid, tables, params, rho)
+    y, T0, _ = _matter(grid, tables, params, rho, p0, D)
+    sD = natural_scale(grid, params, rho, y[0], y[1], ns).ravel()
+    # rounding scale of each entry of vec: G = D - Q_D is formed from terms of size |D|
+    H0 = _outputs(grid, tables, params, rho, p0, D)[4]
+    mag = np.concatenate([np.abs(D).ravel(), np.abs([y[1], y[0], T0]), np.abs(H0).ravel()]) + 1e-300
+    J = np.empty((n, n))
+    dO = np.empty((mag.size - n, n))
+    Dv = D.ravel()
+    for j in range(n):
+        def f(t, j=j):
+            Dp = Dv.copy()
+            Dp[j] += t
+            return vec(p0, Dp.reshape(ns, ne))
+        d = _stencil_refined(f, rel * sD[j], mag)
+        J[:, j] = d[:n]
+        dO[:, j] = d[n:]
+    return J, dO, mag
+
+
+def condition_number(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, scale, D, rel=1e-5):
+    """2-norm condition number of dG/dD at the converged moments D of one node."""
+    p0 = (np.array(D_star, dtype=float), np.array(I_star, dtype=float), float(Ye_star), float(T_star),
+          np.array(scale, dtype=float), float(dt))
+    J, _, _ = _jacobian(grid, tables, params, rho, p0, np.asarray(D, dtype=float), rel)
+    return float(np.linalg.cond(J))
+
+
 def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, scale, D,
              gD=None, gYe=0.0, geps=0.0, gT=0.0, gH=None, rel=1e-5):
     """dL/d(D*, I*, Ye*, T*, scale) at the converged moments D of one node.
 
-    Returns a dict with keys D_star (ns, ne), I_star (ns, ne, 3), Ye, T, scale (4,).
+    Returns a dict with keys D_star (ns, ne), I_star (ns, ne, 3), Ye, T, scale (4,),
+    and two diagnostics of how well the gradient is determined: cond, the
+    2-norm condition number of dG/dD, and mag, for every entry the sum of the
+    absolute terms it is formed from (|g_O| . |dO/dp| + |lambda| . |dG/dp|).
+    An error e in the converged D moves an entry by about cond * |e| * mag.
     """
     ns, ne = D.shape
     n = ns * ne
@@ -130,35 +177,17 @@ def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, sca
 
     gO = np.concatenate([[gYe, geps, gT], gH.ravel()])
 
-    def vec(p, Dm, state=None):
-        """(G, O) at moments Dm for parameters p, as one vector."""
-        G, Ye, eps, T, H = _outputs(grid, tables, params, rho, p, Dm, state)
-        return np.concatenate([G.ravel(), [Ye, eps, T], H.ravel()])
-
-    y, T0, _ = _matter(grid, tables, params, rho, p0, D)
-    sD = natural_scale(grid, params, rho, y[0], y[1], ns).ravel()
-    # rounding scale of each entry of vec: G = D - Q_D is formed from terms of size |D|
-    H0 = _outputs(grid, tables, params, rho, p0, D)[4]
-    mag = np.concatenate([np.abs(D).ravel(), np.abs([y[1], y[0], T0]), np.abs(H0).ravel()]) + 1e-300
-    # dG/dD and dL_x/dD
-    J = np.empty((n, n))
-    dLx = np.empty(n)
-    Dv = D.ravel()
-    for j in range(n):
-        def f(t, j=j):
-            Dp = Dv.copy()
-            Dp[j] += t
-            return vec(p0, Dp.reshape(ns, ne))
-        d = _stencil_refined(f, rel * sD[j], mag)
-        J[:, j] = d[:n]
-        dLx[j] = gD.ravel()[j] + gO @ d[n:]
+    vec = _vec_fn(grid, tables, params, rho)
+    J, dO, mag = _jacobian(grid, tables, params, rho, p0, D, rel)
+    dLx = gD.ravel() + gO @ dO
     lam = np.linalg.solve(J.T, dLx)
 
     def dL_dp(make, h, state=None, refine=False):
-        """dL_x/dp - lambda . dG/dp for one scalar parameter; make(t) returns p with that parameter + t."""
+        """(dL_x/dp - lambda . dG/dp, sum of |terms|) for one scalar parameter;
+        make(t) returns p with that parameter + t."""
         fp = lambda t: vec(make(t), D, state)  # noqa: E731
         d = _stencil_refined(fp, h, mag) if refine else _stencil(fp, h)
-        return gO @ d[n:] - lam @ d[:n]
+        return gO @ d[n:] - lam @ d[:n], np.abs(gO) @ np.abs(d[n:]) + np.abs(lam) @ np.abs(d[:n])
 
     def set_entry(idx, index):
         def make(t):
@@ -174,22 +203,25 @@ def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, sca
 
     ys = (eos.specific_energy(rho, p0[3], p0[2]), p0[2])
     sDs = natural_scale(grid, params, rho, ys[0], ys[1], ns)
-    out_D = np.empty((ns, ne))
+    out, amag = {}, {}
+    out["D_star"], amag["D_star"] = np.empty((ns, ne)), np.empty((ns, ne))
     for s in range(ns):
         for q in range(ne):
-            out_D[s, q] = dL_dp(set_entry(0, (s, q)), rel * sDs[s, q], refine=True)
+            out["D_star"][s, q], amag["D_star"][s, q] = dL_dp(set_entry(0, (s, q)), rel * sDs[s, q], refine=True)
     # I* enters neither q nor the opacities: the matter state at D is shared by its perturbations,
     # and G and the outputs are linear in I*
     state = _matter(grid, tables, params, rho, p0, D)
     hI = rel * max(np.max(np.abs(p0[1])), 1e-300)
-    out_I = np.empty((ns, ne, 3))
+    out["I_star"], amag["I_star"] = np.empty((ns, ne, 3)), np.empty((ns, ne, 3))
     for s in range(ns):
         for q in range(ne):
             for c in range(3):
-                out_I[s, q, c] = dL_dp(set_entry(1, (s, q, c)), hI, state)
-    g_Ye = dL_dp(set_entry(2, None), rel * abs(p0[2]))
-    g_T = dL_dp(set_entry(3, None), rel * abs(p0[3]))
-    g_scale = np.empty(4)
+                out["I_star"][s, q, c], amag["I_star"][s, q, c] = dL_dp(set_entry(1, (s, q, c)), hI, state)
+    out["Ye"], amag["Ye"] = dL_dp(set_entry(2, None), rel * abs(p0[2]))
+    out["T"], amag["T"] = dL_dp(set_entry(3, None), rel * abs(p0[3]))
+    out["scale"], amag["scale"] = np.empty(4), np.empty(4)
     for k in range(4):
-        g_scale[k] = dL_dp(set_entry(4, k), rel * max(abs(p0[4][k]), 1e-3))
-    return dict(D_star=out_D, I_star=out_I, Ye=g_Ye, T=g_T, scale=g_scale)
+        out["scale"][k], amag["scale"][k] = dL_dp(set_entry(4, k), 1e-3 * max(abs(p0[4][k]), 1e-3), refine=True)
+    out["cond"] = float(np.linalg.cond(J))
+    out["mag"] = amag
+    return out

@@ -397,4 +397,32 @@ int opacity_interp(nmc_ctx* ctx, int32_t which, int32_t species, int64_t p, cons
     return launch_opacity_interp(ctx, which, species, p, rho, T, Ye, E, out, static_cast<cudaStream_t>(stream));
 }
 
+int collision_adjoint(nmc_ctx* ctx, const nmc_params* params, int64_t n, const double* rho,
+                      const double* T_in, const double* Ye_in, const double* J_in, const double* H_in,
+                      const double* dt, const double* opac_scale, const double* J_out, const double* T_out,
+                      const double* gJ_out, const double* gH_out, const double* gYe_out,
+                      const double* geps_out, const double* gT_out, double* gJ_in, double* gH_in,
+                      double* gYe_in, double* gT_in, double* gscale, uint32_t* status, void* stream) {
+    if (!ctx) return NMC_EINVAL;
+    int rc = nmc_check_params_internal(ctx, params);
+    if (rc != NMC_OK) return rc;
+    if (n < 0) return set_error(ctx, NMC_EINVAL, "n < 0");
+    if (n == 0) return NMC_OK;
+    if (!rho || !T_in || !Ye_in || !J_in || !dt || !J_out || !gJ_in || !gYe_in || !gT_in)
+        return set_error(ctx, NMC_EINVAL, "null array argument");
+    if (gH_out && !H_in) return set_error(ctx, NMC_EINVAL, "gH_out needs H_in");
+    AdjointArgs a{};
+    a.g = ctx->g;
+    a.tb = ctx->tb;
+    a.p = *params;
+    a.n = n;
+    a.rho = rho; a.T = T_in; a.Ye = Ye_in; a.J = J_in; a.H = H_in; a.dt = dt; a.scale = opac_scale;
+    a.J_out = J_out; a.T_out = T_out;
+    a.gJ = gJ_out; a.gH = gH_out; a.gYe = gYe_out; a.geps = geps_out; a.gT = gT_out;
+    a.gJ_in = gJ_in; a.gH_in = gH_in; a.gYe_in = gYe_in; a.gT_in = gT_in; a.gscale = gscale;
+    a.status = status;
+    a.fd_rel = 1e-6;
+    return launch_adjoint(ctx, a, static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"

@@ -1,0 +1,326 @@
+// Device building blocks shared by the solve and adjoint kernels: block and
+// per-species reductions, table-axis lookup, and ComputeOpacities of
+// Algorithm 1 (EoS chemical potentials, the projected and limited D^Eq of
+// Eq. fermiDiracProjection, EmAb/Iso interpolation, and the NES and pair kernel
+// matrices in shared memory).
+//
+// Thread mapping used throughout: thread (s, q) = s * nep + q owns species s
+// at energy node q; nep is ne padded to a power of two <= 32 or a multiple of
+// 32, so a species group never straddles a warp unevenly.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "nmc_internal.h"
+#include "nmc_eos.cuh"
+
+namespace nmc {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double r_exp(double x) { return exp(x); }
+__device__ __forceinline__ float r_exp(float x) { return expf(x); }
+__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double r_log10(double x) { return log10(x); }
+__device__ __forceinline__ float r_log10(float x) { return log10f(x); }
+
+// Sum K values over the whole block; result in out[0..K).
+template <int K, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[K], void* scratch, T* out) {
+    T* red = static_cast<T*>(scratch);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(kFull, v[k], off);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[w * K + k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        const int nw = blockDim.x >> 5;
+        T s = 0;
+        for (int i = 0; i < nw; ++i) s += red[i * K + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Sum K values over each species group (threads s*nep .. s*nep+nep-1);
+// result in out[s*K + k].  nep is a power of two <= 32 or a multiple of 32.
+template <int K, typename T>
+__device__ __forceinline__ void species_sum(T (&v)[K], void* scratch, T* out, int nep, int ns) {
+    T* red = static_cast<T*>(scratch);
+    const int W = nep < 32 ? nep : 32;
+    for (int off = W >> 1; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(kFull, v[k], off);
+    }
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (nep <= 32) {
+        if ((lane & (W - 1)) == 0) {
+            const int sp = tid / nep;
+            if (sp < ns) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) out[sp * K + k] = v[k];
+            }
+        }
+        __syncthreads();
+    } else {
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) red[w * K + k] = v[k];
+        }
+        __syncthreads();
+        const int wps = nep >> 5;
+        if (tid < ns * K) {
+            const int sp = tid / K, k = tid % K;
+            T s = 0;
+            for (int i = 0; i < wps; ++i) s += red[(sp * wps + i) * K + k];
+            out[sp * K + k] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Cell index and fractional offset of v on a uniform axis, clamped to the
+// table; *clamped is set when v lies outside it.
+template <typename R>
+__device__ __forceinline__ void axis_cell(R v, const Axis& ax, int* i, double* t, int* clamped) {
+    R x = (v - (R)ax.lo) * (R)ax.inv_d;
+    if (!(x >= (R)0)) { *clamped = 1; x = 0; }
+    if (x > (R)(ax.n - 1)) { x = (R)(ax.n - 1); *clamped = 1; }
+    int c = (int)floor((double)x);
+    if (c > ax.n - 2) c = ax.n - 2;
+    *i = c;
+    *t = (double)(x - (R)c);
+}
+
+// Node-wide results of the scalar part of ComputeOpacities (shared memory,
+// written by thread 0).
+struct OpacState {
+    double eta_e;              // mu_e / T
+    double mu[kMaxSpecies];    // neutrino chemical potentials per species
+    double tr, tt, ty, kt, ke; // fractional offsets in the table cells
+    int ir, it, iy, ikt, ike;  // table cells
+};
+
+// Shared-memory operands ComputeOpacities fills.
+template <typename R>
+struct OpacBufs {
+    R* phi;    // [NS][NE][LD] K_Out = dtau (4 pi/(hc)^3) s_NES Phi_Out per species;
+               // also holds the FD values at the projection points while D^Eq is formed
+    R* ann;    // [NS/2][NE][LD] K_Ann = dtau (4 pi/(hc)^3) s_Pair Phi_Ann per pair (particle)
+    R* vA;     // [NS][NEP] a = D^Eq / (1 - D^Eq)
+    R* vAi;    //           1 / a
+    R* vDeq;   //           D^Eq
+    R* vDeqc;  //           1 - D^Eq (mixed precision; FP64 forms it from D^Eq)
+};
+
+// ComputeOpacities of Algorithm 1 at the matter state (rho, T, Ye), called by
+// every thread of the block with the same arguments (sc points to the node's
+// four scale factors EmAb, Iso, NES, Pair).
+//  - Chemical potentials from the EoS (thread 0; FP32 in mixed precision).
+//  - Fermi--Dirac values at the projection quadrature points, the
+//    eps^2-weighted L2 projection and the bound-enforcing limiter per
+//    (species, element) (Eq. fermiDiracProjection).
+//  - chi_EmAb and sigma_Iso by trilinear interpolation of the ln tables in
+//    (log10 rho, log10 T, Ye), each times dtau and its scale: returned in the
+//    calling thread's chiab and sig with its D^Eq (deq) and 1 - D^Eq (deqc).
+//  - The NES kernel K_Out (bilinear in (log10 T, eta_e)) tabulated for
+//    q >= q' and completed by detailed balance, K_Out[q'][q] = a_q / a_q'
+//    K_Out[q][q'] for q' < q (Eqs. inOutInvarianceNES, detailedBalanceNES),
+//    and the pair kernel K_Ann of each particle/antiparticle pair.
+// Thread 0 ORs NMC_TABLE_CLAMP into *status when a lookup leaves a table.
+// Ends with the block synchronised.
+template <typename R>
+__device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const nmc_params& P, double rho,
+                                  double T, double Ye, double dtau, const double* sc, const OpacBufs<R>& b,
+                                  OpacState* os, int* status, R& chiab, R& sig, R& deq, R& deqc) {
+    constexpr bool kMixed = sizeof(R) == 4;
+    const int NS = g.ns, NE = g.ne, NEP = g.nep, LD = g.ld;
+    const int tid = threadIdx.x;
+    const int s = tid / NEP, q = tid - s * NEP;
+    const bool act = (s < NS) && (q < NE);
+    const int sq = s * NEP + q;
+    const bool nes_on = (P.proc_mask & NMC_PROC_NES) != 0;
+    const bool pair_on = (P.proc_mask & NMC_PROC_PAIR) != 0;
+    R* fq = b.phi;
+
+    if (tid == 0) {
+        double mu_e, mnu;
+        if (kMixed) {
+            const EosScaleF es = eos_scale(rho, Ye);
+            const float mf = eos_mu_e_f(es.ne, (float)T);
+            mu_e = mf;
+            mnu = mf - ((float)T * logf((1.0f - (float)Ye) / (float)Ye) + (float)kDmNP);
+        } else {
+            mu_e = eos_mu_e(rho, T, Ye);
+            mnu = mu_e - eos_mu_hat(T, Ye);
+        }
+        os->eta_e = mu_e / T;
+        for (int sp = 0; sp < kMaxSpecies; ++sp) os->mu[sp] = sp == 0 ? mnu : (sp == 1 ? -mnu : 0.0);
+        int cl = 0;
+        axis_cell<R>(r_log10((R)rho), tb.rho, &os->ir, &os->tr, &cl);
+        axis_cell<R>(r_log10((R)T), tb.t, &os->it, &os->tt, &cl);
+        axis_cell<R>((R)Ye, tb.ye, &os->iy, &os->ty, &cl);
+        if (nes_on || pair_on) {
+            axis_cell<R>(r_log10((R)T), tb.kt, &os->ikt, &os->kt, &cl);
+            axis_cell<R>((R)os->eta_e, tb.eta, &os->ike, &os->ke, &cl);
+        }
+        if (cl) *status |= NMC_TABLE_CLAMP;
+    }
+    __syncthreads();
+    // Fermi--Dirac at the projection quadrature points of every element
+    {
+        const int nqp = g.n_elem * kProjQuad;
+        if (s < NS) {
+            const R mu = (R)os->mu[s], Tinv = (R)(1.0 / T);
+            for (int i = q; i < nqp; i += NEP) {
+                if (kMixed) {   // f and 1 - f from one exp, each without cancellation
+                    const R x = ((R)g.proj_e_f[i] - mu) * Tinv;
+                    const R t = r_exp(-fabsf((float)x));
+                    const R inv = (R)1 / ((R)1 + t);
+                    fq[s * nqp + i] = x > 0 ? t * inv : inv;
+                    fq[(NS + s) * nqp + i] = x > 0 ? inv : t * inv;
+                } else {
+                    fq[s * nqp + i] = (R)1 / (r_exp(((R)g.proj_e[i] - mu) * Tinv) + (R)1);
+                }
+            }
+        }
+        __syncthreads();
+        // eps^2-weighted projection and bound-enforcing limiter per (species, element)
+        if (s < NS && q < g.n_elem) {
+            const int e = q, nq = g.nq;
+            const R* f = fq + s * nqp + e * kProjQuad;
+            const R* fc = fq + (NS + s) * nqp + e * kProjQuad;
+            R avg = 0, avgc = 0, coef[kMaxNq] = {0, 0, 0}, coefc[kMaxNq] = {0, 0, 0};
+            for (int gq = 0; gq < kProjQuad; ++gq) {
+                const R pa = kMixed ? (R)g.proj_a_f[e * kProjQuad + gq] : (R)g.proj_a[e * kProjQuad + gq];
+                const R fv = f[gq];
+                avg += pa * fv;
+                R fcv = 0;
+                if (kMixed) { fcv = fc[gq]; avgc += pa * fcv; }
+                for (int pp = 0; pp < nq; ++pp) {
+                    const int o = (e * nq + pp) * kProjQuad + gq;
+                    const R pc = kMixed ? (R)g.proj_c_f[o] : (R)g.proj_c[o];
+                    coef[pp] += pc * fv;
+                    if (kMixed) coefc[pp] += pc * fcv;
+                }
+            }
+            const R dmin = (R)P.d_min, dmax = (R)P.d_max;
+            if (avg < dmin || avg > dmax) {
+                const bool lo = avg < dmin;
+                const R cv = lo ? dmin : dmax;
+                const R cvc = lo ? (R)(1.0 - P.d_min) : (R)(1.0 - P.d_max);
+                for (int pp = 0; pp < nq; ++pp) { coef[pp] = cv; coefc[pp] = cvc; }
+            } else {
+                R vmin = coef[0], vmax = coef[0];
+                for (int pp = 1; pp < nq; ++pp) { vmin = fmin(vmin, coef[pp]); vmax = fmax(vmax, coef[pp]); }
+                for (int side = 0; side < 2; ++side) {
+                    R v = 0;
+                    for (int pp = 0; pp < nq; ++pp) v += coef[pp] * (R)g.ends[side][pp];
+                    vmin = fmin(vmin, v);
+                    vmax = fmax(vmax, v);
+                }
+                R theta = 1;
+                if (vmin < dmin) theta = fmin(theta, (avg - dmin) / (avg - vmin));
+                if (vmax > dmax) theta = fmin(theta, (dmax - avg) / (vmax - avg));
+                for (int pp = 0; pp < nq; ++pp) {
+                    coef[pp] = avg + theta * (coef[pp] - avg);
+                    coefc[pp] = avgc + theta * (coefc[pp] - avgc);
+                }
+            }
+            for (int pp = 0; pp < nq; ++pp) {
+                b.vDeq[s * NEP + e * nq + pp] = coef[pp];
+                b.vDeqc[s * NEP + e * nq + pp] = coefc[pp];
+            }
+        }
+        __syncthreads();
+    }
+    // EmAb / Iso: trilinear in (log10 rho, log10 T, Ye) on ln values, times dtau
+    if (act) {
+        deq = b.vDeq[sq];
+        const R dc = kMixed ? b.vDeqc[sq] : (R)1 - deq;
+        deqc = dc;
+        b.vA[sq] = deq / dc;
+        b.vAi[sq] = dc / deq;
+        const int nr = tb.rho.n, nt = tb.t.n, ny = tb.ye.n;
+        const long long base = ((((long long)s * ny + os->iy) * nt + os->it) * nr + os->ir) * NE + q;
+        const long long dR = NE, dT = (long long)nr * NE, dY = (long long)nt * nr * NE;
+        const R tr = (R)os->tr, tt = (R)os->tt, ty = (R)os->ty;
+        R le = 0, li = 0;
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+            const int ca = c8 & 1, cb = (c8 >> 1) & 1, cc = c8 >> 2;
+            const R w = (ca ? tr : (R)1 - tr) * (cb ? tt : (R)1 - tt) * (cc ? ty : (R)1 - ty);
+            const long long o = base + ca * dR + cb * dT + cc * dY;
+            if (kMixed) { le += w * (R)tb.emab_f[o]; li += w * (R)tb.iso_f[o]; }
+            else { le += w * (R)tb.emab[o]; li += w * (R)tb.iso[o]; }
+        }
+        chiab = (P.proc_mask & NMC_PROC_EMAB) ? (R)(dtau * sc[0]) * r_exp(le) : (R)0;
+        sig = (P.proc_mask & NMC_PROC_ISO) ? (R)(dtau * sc[1]) * r_exp(li) : (R)0;
+    }
+    // NES and pair kernels: bilinear in (log10 T, eta_e), times dtau 4 pi / (hc)^3
+    if (nes_on || pair_on) {
+        const R kt = (R)os->kt, ke = (R)os->ke;
+        const R w00 = ((R)1 - kt) * ((R)1 - ke), w10 = kt * ((R)1 - ke);
+        const R w01 = ((R)1 - kt) * ke, w11 = kt * ke;
+        const long long mat = (long long)NE * NE;
+        const long long sE = mat, sT = (long long)tb.eta.n * mat;
+        const double unit = kMixed ? dtau : dtau * kCW;   // FP32 tables carry 4 pi/(hc)^3
+        if (nes_on && act) {
+            const R c = (R)(unit * sc[2]);
+            const long long off = (((long long)s * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
+            R* P0 = b.phi + s * NE * LD;
+            for (int r = 0; r < NE; ++r) {   // lower triangle incl. diagonal; row r read coalesced
+                if (q <= r) {
+                    const long long o = off + (long long)r * NE + q;
+                    R v;
+                    if (kMixed) {
+                        const float* t = tb.nes_f;
+                        v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
+                    } else {
+                        const double* t = tb.nes;
+                        v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
+                    }
+                    P0[r * LD + q] = c * v;
+                }
+            }
+        }
+        if (pair_on && s < NS) {
+            const int pr = s >> 1;
+            const R c = (R)(unit * sc[3]);
+            const long long off = (((long long)pr * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
+            R* A0 = b.ann + pr * NE * LD;
+            for (int idx = (s & 1) * NEP + q; idx < NE * NE; idx += 2 * NEP) {
+                const int r = idx / NE, cc = idx - r * NE;
+                const long long o = off + idx;
+                R v;
+                if (kMixed) {
+                    const float* t = tb.pair_f;
+                    v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
+                } else {
+                    const double* t = tb.pair;
+                    v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
+                }
+                A0[r * LD + cc] = c * v;
+            }
+        }
+        __syncthreads();
+        if (nes_on && act) {   // up-scattering by detailed balance: K[r][q] = a_q / a_r K[q][r], r < q
+            R* P0 = b.phi + s * NE * LD;
+            const R aq = b.vA[sq];
+            for (int r = 0; r < q; ++r) P0[r * LD + q] = aq * b.vAi[s * NEP + r] * P0[q * LD + r];
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace nmc

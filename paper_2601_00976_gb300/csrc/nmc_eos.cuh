@@ -43,7 +43,7 @@ __device__ __forceinline__ void eos_eps(double rho, double T, double Ye, double*
 
 // T with eps(rho, T, Ye) = eps_t: safeguarded Newton in T, bracketed by
 // [kTMin, kTMax].  *ok = false (and T clamped) when eps_t is outside the range.
-__device__ double eos_temperature(double rho, double eps_t, double Ye, double T0, bool* ok) {
+__device__ inline double eos_temperature(double rho, double eps_t, double Ye, double T0, bool* ok) {
     *ok = true;
     if (!(Ye > 0.0 && Ye < 1.0) || !isfinite(eps_t)) {
         *ok = false;
@@ -67,6 +67,16 @@ __device__ double eos_temperature(double rho, double eps_t, double Ye, double T0
         if (d <= 2e-16 * T || hi - lo <= 4e-16 * hi) break;
     }
     return T;
+}
+
+// d eps / d Ye at fixed rho, T (erg/g): only the electrons depend on Ye, with
+// d n_e / d Ye = rho / m_B and, at fixed T,
+// d u_e / d n_e = (du_e/dmu) / (dn_e/dmu) = 3 mu (mu^2 + pi^2 T^2) / (3 mu^2 + pi^2 T^2).
+__device__ __forceinline__ double eos_deps_dye(double rho, double T, double Ye) {
+    const double pi2 = kPi * kPi;
+    const double mu = eos_mu_e(rho, T, Ye);
+    const double mu2 = mu * mu, T2 = T * T;
+    return kMeVErg / kMB * 3.0 * mu * (mu2 + pi2 * T2) / (3.0 * mu2 + pi2 * T2);
 }
 
 __device__ __forceinline__ double eos_mu_hat(double T, double Ye) {
@@ -114,7 +124,7 @@ __device__ __forceinline__ void eos_u_f(const EosScaleF& sc, float T, float* u, 
 
 // Temperature for the mixed path: bracketed Newton in FP32 to ~1e-7, then one
 // FP64 Newton step on eps(rho, T, Ye), which squares the relative error.
-__device__ double eos_temperature_mixed(double rho, double eps_t, double Ye, double T0, bool* ok) {
+__device__ inline double eos_temperature_mixed(double rho, double eps_t, double Ye, double T0, bool* ok) {
     *ok = true;
     if (!(Ye > 0.0 && Ye < 1.0) || !isfinite(eps_t)) {
         *ok = false;

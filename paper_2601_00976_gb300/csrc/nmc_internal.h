@@ -96,6 +96,37 @@ struct SolveArgs {
     int off_phi, off_ann, off_vec, off_red, off_node;
 };
 
+// Arguments of the adjoint kernel (collision_adjoint).
+struct AdjointArgs {
+    DevGrid g;
+    DevTables tb;
+    nmc_params p;
+    long long n;
+    const double* rho;
+    const double* T;
+    const double* Ye;
+    const double* J;
+    const double* H;
+    const double* dt;
+    const double* scale;
+    const double* J_out;
+    const double* T_out;
+    const double* gJ;
+    const double* gH;
+    const double* gYe;
+    const double* geps;
+    const double* gT;
+    double* gJ_in;
+    double* gH_in;
+    double* gYe_in;
+    double* gT_in;
+    double* gscale;
+    uint32_t* status;
+    double fd_rel;
+    int ldm;   // leading dimension of the augmented pair matrix
+    int off_phi, off_ann, off_mat, off_vec, off_red, off_node;
+};
+
 }  // namespace nmc
 
 struct nmc_ctx {
@@ -119,6 +150,8 @@ int launch_opacity_interp(nmc_ctx* ctx, int which, int species, long long p, con
                           const double* T, const double* Ye, const double* E, double* out,
                           cudaStream_t stream);
 size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, bool mixed, SolveArgs* a);
+int launch_adjoint(nmc_ctx* ctx, AdjointArgs& a, cudaStream_t stream);
+size_t adjoint_smem_bytes(const nmc_ctx* ctx, AdjointArgs* a);
 int set_error(nmc_ctx* ctx, int code, const std::string& msg);
 }  // namespace nmc
 

@@ -47,26 +47,15 @@
 
 #include "nmc_internal.h"
 #include "nmc_eos.cuh"
+#include "nmc_device.cuh"
 
 namespace nmc {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ double r_exp(double x) { return exp(x); }
-__device__ __forceinline__ float r_exp(float x) { return expf(x); }
-__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double r_log10(double x) { return log10(x); }
-__device__ __forceinline__ float r_log10(float x) { return log10f(x); }
-
 template <int MAXM>
 struct NodeShared {
-    double rho, dtau, T, eta_e;
-    double mu[kMaxSpecies];
+    double rho, dtau, T;
     double sc[4];
     double y[2], ystar[2], qv[2];
     double EN_star[2];
@@ -77,73 +66,11 @@ struct NodeShared {
     double dnorm[kMaxSpecies];
     double sp_out[kMaxSpecies * 4];
     double blk_out[8];
-    double tr, tt, ty, kt, ke;
-    int ir, it, iy, ikt, ike;
+    OpacState op;
     long long node;
     int status, n_inner, n_outer;
     int conv_in, conv_out, bad, done;
 };
-
-// Sum K values over the whole block; result in out[0..K).
-template <int K, typename T>
-__device__ __forceinline__ void block_sum(T (&v)[K], void* scratch, T* out) {
-    T* red = static_cast<T*>(scratch);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(kFull, v[k], off);
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) red[w * K + k] = v[k];
-    }
-    __syncthreads();
-    if (threadIdx.x < K) {
-        const int nw = blockDim.x >> 5;
-        T s = 0;
-        for (int i = 0; i < nw; ++i) s += red[i * K + threadIdx.x];
-        out[threadIdx.x] = s;
-    }
-    __syncthreads();
-}
-
-// Sum K values over each species group (threads s*nep .. s*nep+nep-1);
-// result in out[s*K + k].  nep is a power of two <= 32 or a multiple of 32.
-template <int K, typename T>
-__device__ __forceinline__ void species_sum(T (&v)[K], void* scratch, T* out, int nep, int ns) {
-    T* red = static_cast<T*>(scratch);
-    const int W = nep < 32 ? nep : 32;
-    for (int off = W >> 1; off > 0; off >>= 1) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(kFull, v[k], off);
-    }
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (nep <= 32) {
-        if ((lane & (W - 1)) == 0) {
-            const int sp = tid / nep;
-            if (sp < ns) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) out[sp * K + k] = v[k];
-            }
-        }
-        __syncthreads();
-    } else {
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) red[w * K + k] = v[k];
-        }
-        __syncthreads();
-        const int wps = nep >> 5;
-        if (tid < ns * K) {
-            const int sp = tid / K, k = tid % K;
-            T s = 0;
-            for (int i = 0; i < wps; ++i) s += red[(sp * wps + i) * K + k];
-            out[sp * K + k] = s;
-        }
-        __syncthreads();
-    }
-}
 
 // Constrained least squares of Algorithm 1 from the Gram matrix of the
 // window [base, L] (L = newest): alpha_L = 1 - sum of the others, normal
@@ -203,17 +130,6 @@ __device__ void outer_anderson(const double (&fh)[kMaxOuterMem][2], int m, doubl
     anderson_solve<MM>(G, m, beta);
 }
 
-template <typename R>
-__device__ __forceinline__ void axis_cell(R v, const Axis& ax, int* i, double* t, int* clamped) {
-    R x = (v - (R)ax.lo) * (R)ax.inv_d;
-    if (!(x >= (R)0)) { *clamped = 1; x = 0; }
-    if (x > (R)(ax.n - 1)) { x = (R)(ax.n - 1); *clamped = 1; }
-    int c = (int)floor((double)x);
-    if (c > ax.n - 2) c = ax.n - 2;
-    *i = c;
-    *t = (double)(x - (R)c);
-}
-
 }  // namespace
 
 // MAXT: block-size class (threads = ns * nep rounded up to 32 must not exceed
@@ -240,7 +156,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
     R* vDeqc = vDeq + NS * NEP;                        //           1 - D^Eq (mixed)
     void* red = smb + a.off_red;                       // reduction scratch
     NodeShared<MAXM>* nd = reinterpret_cast<NodeShared<MAXM>*>(smb + a.off_node);
-    R* fq = phi;                                       // FD values at projection points (reuses phi)
+    const OpacBufs<R> ob{phi, ann, vA, vAi, vDeq, vDeqc};
 
     const nmc_params& P = a.p;
     const bool nes_on = (P.proc_mask & NMC_PROC_NES) != 0;
@@ -249,9 +165,6 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
     const double W2q = act ? g.w2[q] : 0.0;
     const double W3q = act ? g.w3[q] : 0.0;
     const R Wt = act ? (kMixed ? (R)g.wt_f[q] : (R)g.wt[q]) : (R)0;
-    const double* proj_e = g.proj_e;
-    const double* proj_a = g.proj_a;
-    const double* proj_c = g.proj_c;
 
     // Qh[.][4] holds the complement 1 - Q_D (mixed precision only)
     R Fh[MAXM][4], Qh[MAXM][5];
@@ -334,174 +247,8 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
 
         for (int k = 1;; ++k) {
             // ================= ComputeOpacities(y^[k]) =================
-            if (tid == 0) {
-                const double T = nd->T, Ye = nd->y[1], rho = nd->rho;
-                double mu_e, mnu;
-                if (kMixed) {
-                    const EosScaleF sc = eos_scale(rho, Ye);
-                    const float mf = eos_mu_e_f(sc.ne, (float)T);
-                    mu_e = mf;
-                    mnu = mf - ((float)T * logf((1.0f - (float)Ye) / (float)Ye) + (float)kDmNP);
-                } else {
-                    mu_e = eos_mu_e(rho, T, Ye);
-                    mnu = mu_e - eos_mu_hat(T, Ye);
-                }
-                nd->eta_e = mu_e / T;
-                for (int sp = 0; sp < kMaxSpecies; ++sp) nd->mu[sp] = sp == 0 ? mnu : (sp == 1 ? -mnu : 0.0);
-                int cl = 0;
-                axis_cell<R>(r_log10((R)rho), a.tb.rho, &nd->ir, &nd->tr, &cl);
-                axis_cell<R>(r_log10((R)T), a.tb.t, &nd->it, &nd->tt, &cl);
-                axis_cell<R>((R)Ye, a.tb.ye, &nd->iy, &nd->ty, &cl);
-                if (nes_on || pair_on) {
-                    axis_cell<R>(r_log10((R)T), a.tb.kt, &nd->ikt, &nd->kt, &cl);
-                    axis_cell<R>((R)nd->eta_e, a.tb.eta, &nd->ike, &nd->ke, &cl);
-                }
-                if (cl) nd->status |= NMC_TABLE_CLAMP;
-            }
-            __syncthreads();
-            // Fermi--Dirac at the projection quadrature points of every element
-            {
-                const int nqp = g.n_elem * kProjQuad;
-                if (s < NS) {
-                    const R mu = (R)nd->mu[s], Tinv = (R)(1.0 / nd->T);
-                    for (int i = q; i < nqp; i += NEP) {
-                        if (kMixed) {   // f and 1 - f from one exp, each without cancellation
-                            const R x = ((R)g.proj_e_f[i] - mu) * Tinv;
-                            const R t = r_exp(-fabsf((float)x));
-                            const R inv = (R)1 / ((R)1 + t);
-                            fq[s * nqp + i] = x > 0 ? t * inv : inv;
-                            fq[(NS + s) * nqp + i] = x > 0 ? inv : t * inv;
-                        } else {
-                            fq[s * nqp + i] = (R)1 / (r_exp(((R)proj_e[i] - mu) * Tinv) + (R)1);
-                        }
-                    }
-                }
-                __syncthreads();
-                // eps^2-weighted projection and bound-enforcing limiter per (species, element)
-                if (s < NS && q < g.n_elem) {
-                    const int e = q, nq = g.nq;
-                    const R* f = fq + s * nqp + e * kProjQuad;
-                    const R* fc = fq + (NS + s) * nqp + e * kProjQuad;
-                    R avg = 0, avgc = 0, coef[kMaxNq] = {0, 0, 0}, coefc[kMaxNq] = {0, 0, 0};
-                    for (int gq = 0; gq < kProjQuad; ++gq) {
-                        const R pa = kMixed ? (R)g.proj_a_f[e * kProjQuad + gq] : (R)proj_a[e * kProjQuad + gq];
-                        const R fv = f[gq];
-                        avg += pa * fv;
-                        R fcv = 0;
-                        if (kMixed) { fcv = fc[gq]; avgc += pa * fcv; }
-                        for (int pp = 0; pp < nq; ++pp) {
-                            const int o = (e * nq + pp) * kProjQuad + gq;
-                            const R pc = kMixed ? (R)g.proj_c_f[o] : (R)proj_c[o];
-                            coef[pp] += pc * fv;
-                            if (kMixed) coefc[pp] += pc * fcv;
-                        }
-                    }
-                    const R dmin = (R)P.d_min, dmax = (R)P.d_max;
-                    if (avg < dmin || avg > dmax) {
-                        const bool lo = avg < dmin;
-                        const R cv = lo ? dmin : dmax;
-                        const R cvc = lo ? (R)(1.0 - P.d_min) : (R)(1.0 - P.d_max);
-                        for (int pp = 0; pp < nq; ++pp) { coef[pp] = cv; coefc[pp] = cvc; }
-                    } else {
-                        R vmin = coef[0], vmax = coef[0];
-                        for (int pp = 1; pp < nq; ++pp) { vmin = fmin(vmin, coef[pp]); vmax = fmax(vmax, coef[pp]); }
-                        for (int side = 0; side < 2; ++side) {
-                            R v = 0;
-                            for (int pp = 0; pp < nq; ++pp) v += coef[pp] * (R)g.ends[side][pp];
-                            vmin = fmin(vmin, v);
-                            vmax = fmax(vmax, v);
-                        }
-                        R theta = 1;
-                        if (vmin < dmin) theta = fmin(theta, (avg - dmin) / (avg - vmin));
-                        if (vmax > dmax) theta = fmin(theta, (dmax - avg) / (vmax - avg));
-                        for (int pp = 0; pp < nq; ++pp) {
-                            coef[pp] = avg + theta * (coef[pp] - avg);
-                            coefc[pp] = avgc + theta * (coefc[pp] - avgc);
-                        }
-                    }
-                    for (int pp = 0; pp < nq; ++pp) {
-                        vDeq[s * NEP + e * nq + pp] = coef[pp];
-                        vDeqc[s * NEP + e * nq + pp] = coefc[pp];
-                    }
-                }
-                __syncthreads();
-            }
-            // EmAb / Iso: trilinear in (log10 rho, log10 T, Ye) on ln values, times dtau
-            if (act) {
-                deq = vDeq[sq];
-                const R dc = kMixed ? vDeqc[sq] : (R)1 - deq;
-                deqc = dc;
-                vA[sq] = deq / dc;
-                vAi[sq] = dc / deq;
-                const int nr = a.tb.rho.n, nt = a.tb.t.n, ny = a.tb.ye.n;
-                const long long base = ((((long long)s * ny + nd->iy) * nt + nd->it) * nr + nd->ir) * NE + q;
-                const long long dR = NE, dT = (long long)nr * NE, dY = (long long)nt * nr * NE;
-                const R tr = (R)nd->tr, tt = (R)nd->tt, ty = (R)nd->ty;
-                R le = 0, li = 0;
-#pragma unroll
-                for (int c8 = 0; c8 < 8; ++c8) {
-                    const int ca = c8 & 1, cb = (c8 >> 1) & 1, cc = c8 >> 2;
-                    const R w = (ca ? tr : (R)1 - tr) * (cb ? tt : (R)1 - tt) * (cc ? ty : (R)1 - ty);
-                    const long long o = base + ca * dR + cb * dT + cc * dY;
-                    if (kMixed) { le += w * (R)a.tb.emab_f[o]; li += w * (R)a.tb.iso_f[o]; }
-                    else { le += w * (R)a.tb.emab[o]; li += w * (R)a.tb.iso[o]; }
-                }
-                chiab = (P.proc_mask & NMC_PROC_EMAB) ? (R)(nd->dtau * nd->sc[0]) * r_exp(le) : (R)0;
-                sig = (P.proc_mask & NMC_PROC_ISO) ? (R)(nd->dtau * nd->sc[1]) * r_exp(li) : (R)0;
-            }
-            // NES and pair kernels: bilinear in (log10 T, eta_e), times dtau 4 pi / (hc)^3
-            if (nes_on || pair_on) {
-                const R kt = (R)nd->kt, ke = (R)nd->ke;
-                const R w00 = ((R)1 - kt) * ((R)1 - ke), w10 = kt * ((R)1 - ke);
-                const R w01 = ((R)1 - kt) * ke, w11 = kt * ke;
-                const long long mat = (long long)NE * NE;
-                const long long sE = mat, sT = (long long)a.tb.eta.n * mat;
-                const double unit = kMixed ? nd->dtau : nd->dtau * kCW;   // FP32 tables carry 4 pi/(hc)^3
-                if (nes_on && act) {
-                    const R c = (R)(unit * nd->sc[2]);
-                    const long long off = (((long long)s * a.tb.kt.n + nd->ikt) * a.tb.eta.n + nd->ike) * mat;
-                    R* P0 = phi + s * NE * LD;
-                    for (int r = 0; r < NE; ++r) {   // lower triangle incl. diagonal; row r read coalesced
-                        if (q <= r) {
-                            const long long o = off + (long long)r * NE + q;
-                            R v;
-                            if (kMixed) {
-                                const float* tb = a.tb.nes_f;
-                                v = w00 * tb[o] + w10 * tb[o + sT] + w01 * tb[o + sE] + w11 * tb[o + sT + sE];
-                            } else {
-                                const double* tb = a.tb.nes;
-                                v = w00 * tb[o] + w10 * tb[o + sT] + w01 * tb[o + sE] + w11 * tb[o + sT + sE];
-                            }
-                            P0[r * LD + q] = c * v;
-                        }
-                    }
-                }
-                if (pair_on && s < NS) {
-                    const int pr = s >> 1;
-                    const R c = (R)(unit * nd->sc[3]);
-                    const long long off = (((long long)pr * a.tb.kt.n + nd->ikt) * a.tb.eta.n + nd->ike) * mat;
-                    R* A0 = ann + pr * NE * LD;
-                    for (int idx = (s & 1) * NEP + q; idx < NE * NE; idx += 2 * NEP) {
-                        const int r = idx / NE, cc = idx - r * NE;
-                        const long long o = off + idx;
-                        R v;
-                        if (kMixed) {
-                            const float* tb = a.tb.pair_f;
-                            v = w00 * tb[o] + w10 * tb[o + sT] + w01 * tb[o + sE] + w11 * tb[o + sT + sE];
-                        } else {
-                            const double* tb = a.tb.pair;
-                            v = w00 * tb[o] + w10 * tb[o + sT] + w01 * tb[o + sE] + w11 * tb[o + sT + sE];
-                        }
-                        A0[r * LD + cc] = c * v;
-                    }
-                }
-                __syncthreads();
-                if (nes_on && act) {   // up-scattering by detailed balance: K[r][q] = a_q / a_r K[q][r], r < q
-                    R* P0 = phi + s * NE * LD;
-                    const R aq = vA[sq];
-                    for (int r = 0; r < q; ++r) P0[r * LD + q] = aq * vAi[s * NEP + r] * P0[q * LD + r];
-                }
-            }
+            compute_opacities<R>(g, a.tb, P, nd->rho, nd->T, nd->y[1], nd->dtau, nd->sc, ob, &nd->op,
+                                 &nd->status, chiab, sig, deq, deqc);
             // reference norm ||D^[k,1]||_W per species (Algorithm 2 input)
             {
                 R v[1] = {Wt * M[0] * M[0]};

@@ -2,7 +2,10 @@
 the collision solve runs in the library's CUDA kernels.
 
 The names follow the C ABI in include/nmc.h: ``Context.collision_solve``,
-``Context.opacity_interp``; ``Context`` wraps ``nmc_create``/``nmc_destroy``.
+``Context.collision_adjoint``, ``Context.opacity_interp``; ``Context`` wraps
+``nmc_create``/``nmc_destroy``.  ``CollisionSolve`` (in
+``paper_2601_00976_gb300.autograd``) is the torch.autograd.Function whose
+backward calls ``collision_adjoint``.
 PyTorch provides device memory and streams.  There is no CPU fallback: if the
 shared library is missing or no CUDA device is present the calls raise.
 """
@@ -54,7 +57,7 @@ class Params(ctypes.Structure):
 
 EXPORTS = ("nmc_default_params", "nmc_create", "nmc_destroy", "nmc_last_error", "nmc_energy_nodes",
            "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "collision_solve_noalloc",
-           "opacity_interp")
+           "opacity_interp", "collision_adjoint")
 
 _lib = None
 
@@ -88,6 +91,8 @@ def load_library(path=LIB_PATH):
     lib.collision_solve_noalloc.restype = ctypes.c_int
     lib.opacity_interp.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64] + [vp] * 6
     lib.opacity_interp.restype = ctypes.c_int
+    lib.collision_adjoint.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 20
+    lib.collision_adjoint.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -230,6 +235,37 @@ class Context:
         self._check(rc, "collision_solve")
         if host:
             out = {k: v.to("cpu", non_blocking=False) for k, v in out.items()}
+        return out
+
+    def collision_adjoint(self, params, rho, T, Ye, J, H, dt, scale, J_out, T_out=None,
+                          gJ=None, gH=None, gYe=None, geps=None, gT=None, out=None, stream=None):
+        """Run collision_adjoint on CUDA float64 tensors.
+
+        Inputs are the forward call's inputs and its converged J_out (T_out
+        optional, the EoS starting guess) plus cotangents of the outputs (any
+        may be None).  Returns a dict of input cotangents J, H, Ye, T, scale
+        and the per-node status.
+        """
+        import torch
+        for x in (rho, T, Ye, J, H, dt, scale, J_out, T_out, gJ, gH, gYe, geps, gT):
+            if x is not None and (x.dtype != torch.float64 or not x.is_contiguous() or not x.is_cuda):
+                raise ValueError("adjoint arguments must be contiguous CUDA float64 tensors")
+        n = rho.shape[0]
+        ns, ne = self.n_species, self.ne
+        if J.shape != (n, ns, ne) or J_out.shape != (n, ns, ne) or (H is not None and H.shape != (n, ns, ne, 3)):
+            raise ValueError(f"J, J_out must be {(n, ns, ne)} and H {(n, ns, ne, 3)}")
+        if out is None:
+            f64 = dict(dtype=torch.float64, device=rho.device)
+            out = dict(J=torch.empty_like(J), H=torch.empty((n, ns, ne, 3), **f64), Ye=torch.empty(n, **f64),
+                       T=torch.empty(n, **f64), scale=torch.empty((n, 4), **f64),
+                       status=torch.empty(n, dtype=torch.int32, device=rho.device))
+        p = lambda x: ctypes.c_void_p(x.data_ptr()) if x is not None else None  # noqa: E731
+        rc = self._lib.collision_adjoint(
+            self._h, ctypes.byref(params), n, p(rho), p(T), p(Ye), p(J), p(H), p(dt), p(scale),
+            p(J_out), p(T_out), p(gJ), p(gH), p(gYe), p(geps), p(gT),
+            p(out["J"]), p(out["H"]), p(out["Ye"]), p(out["T"]), p(out["scale"]), p(out["status"]),
+            self._stream_handle(stream))
+        self._check(rc, "collision_adjoint")
         return out
 
     def opacity_interp(self, which, species, rho, T, Ye, E, out=None, stream=None):
