@@ -9,6 +9,10 @@ Inputs (J, H of 268 MB) are larger than L2, so every step reads them from HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nmc|reference]
 
+The same line carries an "adjoint" object: collision_adjoint (gradients of
+every output with respect to the inputs and the opacity scale factors, FP64)
+over 2^18 nodes of the same profile and grid, timed the same way.
+
 Prints one JSON line.  --impl reference times the CPU oracle (the plain FP64
 restatement of the algorithm) on a bounded sample of the same workload.
 """
@@ -33,8 +37,16 @@ N_ELEM, DE1, NQ, NS = 16, 1.875, 2, 4
 TOL, MEM = 1e-10, 3
 WORKLOAD = ("collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, EmAb+Iso+NES+pair, "
             "FP64, Anderson depth 3, tol 1e-10")
+# DRAM bytes (read + write) per node of one launch, from ncu captures of the 2^16-node profile
+# (dram__bytes_read.sum + dram__bytes_write.sum); traffic grows with the node count
+TRAFFIC_PER_NODE = {"fused_kernel<double>": 527294720 / 65536, "fused_kernel<float>": 512146944 / 65536,
+                    "adjoint_kernel": 875269376 / 65536}
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64: 152 SMs x 4 flop/clk x 2.07 GHz (recipe unit count and clock)
 CPU_SAMPLE = 48           # oracle sample (nodes) for the CPU baseline
+ADJ_NODES = 1 << 18
+ADJ_WORKLOAD = ("gradient of the FP64 solve (collapse profile, 2^18 nodes, 4 species, Grid C 16x2 energies, "
+                "all processes, forward tol 1e-10) w.r.t. J, H, Ye, T and the 4 opacity scales, "
+                "cotangents on J, H, Ye, eps, T")
 
 
 def _args():
@@ -44,6 +56,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nmc", choices=["nmc", "reference"])
     ap.add_argument("--nodes", type=int, default=N_NODES)
+    ap.add_argument("--adjoint-nodes", type=int, default=ADJ_NODES, help="0 skips the adjoint measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="path reported as the headline value (both are timed)")
@@ -195,6 +208,50 @@ def _time_path(ctx, prm, t, out, steps, warmup, barrier, stream):
     return per_step, total_ms
 
 
+def time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream):
+    """Time collision_adjoint over the adjoint workload (inputs and cotangents resident in HBM)."""
+    import torch
+    from paper_2601_00976_gb300 import nmc, synthetic, flops
+    n = args.adjoint_nodes
+    inp = synthetic.make_inputs("profile", n, eps, NS, seed=1000 + rank)
+    t = {k: torch.tensor(v, device=dev) for k, v in inp.items()}
+    p = nmc.default_params(tol_inner=TOL, tol_outer=TOL, m_inner=MEM, m_outer=MEM)
+    fw = ctx.collision_solve(p, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+    gen = torch.Generator(device=dev).manual_seed(77 + rank)
+    f64 = dict(dtype=torch.float64, device=dev, generator=gen)
+    ct = dict(gJ=torch.randn(t["D"].shape, **f64), gH=torch.randn(t["I"].shape, **f64),
+              gYe=torch.randn(n, **f64), geps=torch.randn(n, **f64) * 1e-19, gT=torch.randn(n, **f64))
+    out = ctx.collision_adjoint(p, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"], fw["J"], fw["T"],
+                                **ct)
+
+    def step():
+        ctx.collision_adjoint(p, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"], fw["J"], fw["T"],
+                              out=out, **ct)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    barrier()
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    total_ms = allmax(evs[0][0].elapsed_time(evs[-1][1]))
+    clean = int(torch.count_nonzero((out["status"] & ~nmc.TABLE_CLAMP) == 0).item())
+    fl = flops.adjoint_flops(NS, len(eps), N_ELEM, NQ) * n
+    ach = fl / (kern_ms * 1e-3) / 1e12
+    return {"metric": "node gradients/s (nodes*steps/s)", "value": n * args.steps / (total_ms * 1e-3),
+            "unit": "nodes/s", "ms_per_step": total_ms / args.steps, "dtype": "f64",
+            "config": {"workload": ADJ_WORKLOAD, "nodes_per_gpu": n, "clean_fraction": clean / n},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_NODE["adjoint_kernel"] * n,
+                         "kernel": "adjoint_kernel",
+                         "peak_source": "derived FP64 FMA rate at 2.07 GHz",
+                         "algorithmic_flops_per_launch": fl, "kernel_ms": kern_ms}}
+
+
 def run_nmc(args):
     import torch
     from paper_2601_00976_gb300 import nmc, flops
@@ -277,6 +334,8 @@ def run_nmc(args):
     barrier()
     e2e_s = allmax((time.perf_counter() - t0) / e2e_steps)
 
+    adj = time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.adjoint_nodes > 0 else None
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(edges, tables, inp)
@@ -287,7 +346,7 @@ def run_nmc(args):
         def roof(r, peak, kernel, note):
             ach = r["flops"] / (r["kern_ms"] * 1e-3) / 1e12
             return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": None, "kernel": kernel, "peak_source": note,
+                    "traffic": TRAFFIC_PER_NODE[kernel] * args.nodes, "kernel": kernel, "peak_source": note,
                     "algorithmic_flops_per_launch": r["flops"], "kernel_ms": r["kern_ms"]}
 
         r64, rmx = res["fp64"], res["mixed"]
@@ -318,6 +377,8 @@ def run_nmc(args):
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
         }
+        if adj is not None:
+            line["adjoint"] = adj
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -41,3 +41,24 @@ def node_flops(ns, ne, n_elem, nq, m, n_inner, n_outer, nes=True, pair=True):
     """Total flops of one node given its inner and outer iteration counts (arrays ok)."""
     return (n_inner * inner_flops(ns, ne, m, nes, pair) + n_outer * outer_flops(ns, ne, n_elem, nq, nes, pair)
             + 600 + 4 * ns * ne)
+
+
+def adjoint_flops(ns, ne, n_elem, nq, with_h=True):
+    """Algorithmic flops of one node's gradient by the adjoint kernel.
+
+    five ComputeOpacities passes (the matter state and its four central-difference
+    neighbours in eps and Ye), each with its EoS root find   -> 5 outer_flops
+    five unit-scale rate evaluations (4 mat-vecs per species) and map values
+                                                              -> 5 (8 ns ne^2 + 20 ns ne)
+    dQ_D/dD rows from the kernel matrices (NES 8, pair 10 per entry) -> 18 ns ne^2
+    dkappa/dD^T g_kappa (NES 3, pair 5 per entry, with an H cotangent) -> 8 ns ne^2
+    per particle/antiparticle pair, Gaussian elimination of an n x n block with
+    three right-hand sides and the back substitutions, n = 2 ne
+                                                              -> (ns/2) (2/3 n^3 + 6 n^2)
+    Woodbury update, reductions and outputs                   -> 30 ns ne
+    """
+    n2 = 2 * ne
+    f = 5 * outer_flops(ns, ne, n_elem, nq) + 5 * (8 * ns * ne * ne + 20 * ns * ne)
+    f += 18 * ns * ne * ne + (8 * ns * ne * ne if with_h else 0)
+    f += (ns // 2) * (2 * n2 ** 3 // 3 + 6 * n2 * n2)
+    return f + 30 * ns * ne
