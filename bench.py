@@ -185,7 +185,10 @@ def cpu_baseline(edges, tables, inp):
 
 
 FP32_PEAK_TFLOPS = 80.6   # dense FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (recipe unit count and clock)
-MIXED_TOL = (1e-6, 1e-7)  # inner, outer tolerances reachable in FP32
+# inner, outer tolerances of the mixed path: where dtau chi ~ 1e4 the heavy flavours' number-conserving
+# mode keeps an error ~ tol (1 + dtau chi), so the stated <= 1e-5 error needs tol ~ 1e-9 (measured max
+# D error against the FP64 path on this workload: 4.6e-7; at 1e-6 it is 1.1e-3)
+MIXED_TOL = (1e-9, 1e-9)
 
 
 def _time_path(ctx, prm, t, out, steps, warmup, barrier, stream):

@@ -156,23 +156,29 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
     if (tid == 0) {
         double mu_e, mnu;
         if (kMixed) {
+            // FP32 root of the electron cubic, then one FP64 Newton step on it (the error
+            // squares): mu_e, and with it D^Eq, must move smoothly with (T, Ye), or the outer
+            // iteration's map is noisy at the 1e-7 level and stalls above tol_outer
             const EosScaleF es = eos_scale(rho, Ye);
-            const float mf = eos_mu_e_f(es.ne, (float)T);
-            mu_e = mf;
-            mnu = mf - ((float)T * logf((1.0f - (float)Ye) / (float)Ye) + (float)kDmNP);
+            const double m0 = eos_mu_e_f(es.ne, (float)T);
+            const double pi2T2 = kPi * kPi * T * T;
+            const double ned = Ye * rho / kMB * (kHbarC * kHbarC * kHbarC);   // FP64 target
+            const double cub = m0 * (m0 * m0 + pi2T2) - 3.0 * kPi * kPi * ned;
+            mu_e = m0 - cub / (3.0 * m0 * m0 + pi2T2);
+            mnu = mu_e - eos_mu_hat(T, Ye);
         } else {
             mu_e = eos_mu_e(rho, T, Ye);
             mnu = mu_e - eos_mu_hat(T, Ye);
         }
         os->eta_e = mu_e / T;
         for (int sp = 0; sp < kMaxSpecies; ++sp) os->mu[sp] = sp == 0 ? mnu : (sp == 1 ? -mnu : 0.0);
-        int cl = 0;
-        axis_cell<R>(r_log10((R)rho), tb.rho, &os->ir, &os->tr, &cl);
-        axis_cell<R>(r_log10((R)T), tb.t, &os->it, &os->tt, &cl);
-        axis_cell<R>((R)Ye, tb.ye, &os->iy, &os->ty, &cl);
+        int cl = 0;   // table cells in FP64 in both precisions (one thread, a few operations)
+        axis_cell<double>(log10(rho), tb.rho, &os->ir, &os->tr, &cl);
+        axis_cell<double>(log10(T), tb.t, &os->it, &os->tt, &cl);
+        axis_cell<double>(Ye, tb.ye, &os->iy, &os->ty, &cl);
         if (nes_on || pair_on) {
-            axis_cell<R>(r_log10((R)T), tb.kt, &os->ikt, &os->kt, &cl);
-            axis_cell<R>((R)os->eta_e, tb.eta, &os->ike, &os->ke, &cl);
+            axis_cell<double>(log10(T), tb.kt, &os->ikt, &os->kt, &cl);
+            axis_cell<double>(os->eta_e, tb.eta, &os->ike, &os->ke, &cl);
         }
         if (cl) *status |= NMC_TABLE_CLAMP;
     }
@@ -182,13 +188,20 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         const int nqp = g.n_elem * kProjQuad;
         if (s < NS) {
             const R mu = (R)os->mu[s], Tinv = (R)(1.0 / T);
+            const double mud = os->mu[s], Tinvd = 1.0 / T;
             for (int i = q; i < nqp; i += NEP) {
-                if (kMixed) {   // f and 1 - f from one exp, each without cancellation
-                    const R x = ((R)g.proj_e_f[i] - mu) * Tinv;
-                    const R t = r_exp(-fabsf((float)x));
+                if (kMixed) {
+                    // f and 1 - f from one exp, each without cancellation.  x = (E - mu)/T reaches
+                    // ~100 in the tail, where rounding x to FP32 would move exp(-|x|) by ~1e-5 in
+                    // steps; x is formed in FP64 and split, e^-|x| = expf(-|x_hi|) (1 - |x|_lo)
+                    const double xd = (g.proj_e[i] - mud) * Tinvd;
+                    const double ax = fabs(xd);
+                    const float xh = (float)ax;
+                    const float xl = (float)(ax - (double)xh);
+                    const R t = r_exp(-xh) * (1.0f - xl);
                     const R inv = (R)1 / ((R)1 + t);
-                    fq[s * nqp + i] = x > 0 ? t * inv : inv;
-                    fq[(NS + s) * nqp + i] = x > 0 ? inv : t * inv;
+                    fq[s * nqp + i] = xd > 0 ? t * inv : inv;
+                    fq[(NS + s) * nqp + i] = xd > 0 ? inv : t * inv;
                 } else {
                     fq[s * nqp + i] = (R)1 / (r_exp(((R)g.proj_e[i] - mu) * Tinv) + (R)1);
                 }
@@ -255,15 +268,21 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         const long long base = ((((long long)s * ny + os->iy) * nt + os->it) * nr + os->ir) * NE + q;
         const long long dR = NE, dT = (long long)nr * NE, dY = (long long)nt * nr * NE;
         const R tr = (R)os->tr, tt = (R)os->tt, ty = (R)os->ty;
+        // ln chi as the first corner plus weighted differences: the corners are ~ -20, so an
+        // FP32 sum of the corner values themselves would round ln chi by ~2e-6 in steps
+        const R le0 = kMixed ? (R)tb.emab_f[base] : (R)tb.emab[base];
+        const R li0 = kMixed ? (R)tb.iso_f[base] : (R)tb.iso[base];
         R le = 0, li = 0;
 #pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) {
+        for (int c8 = 1; c8 < 8; ++c8) {
             const int ca = c8 & 1, cb = (c8 >> 1) & 1, cc = c8 >> 2;
             const R w = (ca ? tr : (R)1 - tr) * (cb ? tt : (R)1 - tt) * (cc ? ty : (R)1 - ty);
             const long long o = base + ca * dR + cb * dT + cc * dY;
-            if (kMixed) { le += w * (R)tb.emab_f[o]; li += w * (R)tb.iso_f[o]; }
-            else { le += w * (R)tb.emab[o]; li += w * (R)tb.iso[o]; }
+            if (kMixed) { le += w * ((R)tb.emab_f[o] - le0); li += w * ((R)tb.iso_f[o] - li0); }
+            else { le += w * ((R)tb.emab[o] - le0); li += w * ((R)tb.iso[o] - li0); }
         }
+        le += le0;
+        li += li0;
         chiab = (P.proc_mask & NMC_PROC_EMAB) ? (R)(dtau * sc[0]) * r_exp(le) : (R)0;
         sig = (P.proc_mask & NMC_PROC_ISO) ? (R)(dtau * sc[1]) * r_exp(li) : (R)0;
     }

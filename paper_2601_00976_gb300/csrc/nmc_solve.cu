@@ -53,6 +53,9 @@ namespace nmc {
 
 namespace {
 
+// Finest relative change of an FP32 moment the mixed path checks (4 ulp of 1).
+constexpr double kFp32Resolution = 4.0 * 1.1920928955078125e-7;
+
 template <int MAXM>
 struct NodeShared {
     double rho, dtau, T;
@@ -154,6 +157,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
     R* vAi = vA + NS * NEP;                            //           1 / a
     R* vDeq = vAi + NS * NEP;                          //           D^Eq
     R* vDeqc = vDeq + NS * NEP;                        //           1 - D^Eq (mixed)
+    R* vWdev = vDeqc + NS * NEP;                        //           w = W~ (D - D^Eq) / (1 - D^Eq) (mixed)
     void* red = smb + a.off_red;                       // reduction scratch
     NodeShared<MAXM>* nd = reinterpret_cast<NodeShared<MAXM>*>(smb + a.off_node);
     const OpacBufs<R> ob{phi, ann, vA, vAi, vDeq, vDeqc};
@@ -166,15 +170,20 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
     const double W3q = act ? g.w3[q] : 0.0;
     const R Wt = act ? (kMixed ? (R)g.wt_f[q] : (R)g.wt[q]) : (R)0;
 
-    // Qh[.][4] holds the complement 1 - Q_D (mixed precision only)
-    R Fh[MAXM][4], Qh[MAXM][5];
+    // Mixed precision keeps the number moment D and its map values in FP64
+    // (QhD): near a fixed point where 1 + dtau chi ~ 1e4, FP32 increments of D
+    // fall below one ulp long before the equation residual is small.
+    R Fh[MAXM][4], Qh[MAXM][4];
+    double QhD[kMixed ? MAXM : 1];
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) Fh[j][c] = 0;
 #pragma unroll
-        for (int c = 0; c < 5; ++c) Qh[j][c] = 0;
+        for (int c = 0; c < 4; ++c) Qh[j][c] = 0;
     }
+#pragma unroll
+    for (int j = 0; j < (kMixed ? MAXM : 1); ++j) QhD[j] = 0.0;
 
     for (;;) {
         if (tid == 0) nd->node = atomicAdd(a.queue, 1);
@@ -235,13 +244,9 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
             if (tid == 0) { nd->EN_star[0] = nd->blk_out[0]; nd->EN_star[1] = nd->blk_out[1]; }
         }
         const R Ds = (R)Dsd;
-        const R Dsc = (R)(1.0 - Dsd);   // 1 - D*, formed in FP64
         const R Is[3] = {(R)Isd[0], (R)Isd[1], (R)Isd[2]};
         R M[4] = {Ds, Is[0], Is[1], Is[2]};
-        // Mixed precision carries the blocking factor 1 - D as its own iterate:
-        // 1 - D in FP32 loses all digits for degenerate D ~ 1 - 1e-6, and the
-        // pair emissivity multiplies it by a = D^Eq/(1 - D^Eq) ~ 1e6.
-        R Dc = Dsc;
+        double Dd = Dsd;   // FP64 number moment (mixed precision); M[0] is its FP32 shadow
         R chiab = 0, sig = 0, deq = 0, deqc = 0;
         int outer_exit = 0;
 
@@ -262,33 +267,44 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
             // ================= inner loop =================
             for (int ell = 1;; ++ell) {
                 if (act) {
-                    const R hole = kMixed ? Dc : (R)1 - M[0];
+                    // mixed: the blocking factor 1 - D and the deviation D - D^Eq are formed from
+                    // the FP64 D (1 - D in FP32 has no digits left at D ~ 1 - 1e-6)
+                    const R hole = kMixed ? (R)(1.0 - Dd) : (R)1 - M[0];
                     vWD[sq] = Wt * M[0];
                     vW1D[sq] = Wt * hole;
                     vAW1D[sq] = vA[sq] * Wt * hole;
+                    if constexpr (kMixed) vWdev[sq] = (R)(Dd - (double)deq) * (Wt / deqc);
                 }
                 __syncthreads();
-                R F[4] = {0, 0, 0, 0}, Qv[5] = {0, 0, 0, 0, 0};
+                R F[4] = {0, 0, 0, 0}, Qv[4] = {0, 0, 0, 0};
+                double QD = 0.0;   // mixed: Q_D in FP64
+                R dlt = 0;         // mixed: Q_D - D, formed without cancellation
                 if (act) {
                     R nin = 0, nout = 0, pro = 0, an = 0;
-                    R cn = 0, cp = 0;   // mixed: net NES / pair terms from pairwise exchanges
+                    R cn = 0, cp = 0;   // mixed: net NES / pair exchange terms (deviation form)
                     if (nes_on) {
                         const R* P0 = phi + s * NE * LD;
                         const R* x = vWD + s * NEP;
                         const R* y = vW1D + s * NEP;
-                        if (kMixed) {
-                            // exchange j -> q is K[j][q] (u_j v_q), q -> j is K[q][j] (u_q v_j), with
-                            // u = W~ D, v = W~ (1 - D); each product is formed with the same
-                            // operands in the two bins it couples, so the exchanges cancel
-                            // exactly in the number sum and NES conserves number to the
-                            // rounding of the net term (not of the gross rates).
-                            const R uq = x[q], vq = y[q];
+                        if constexpr (kMixed) {
+                            // Net exchange with bin j: K[j][q] u_j v_q - K[q][j] u_q v_j, u = W~ D,
+                            // v = W~ (1 - D).  With detailed balance K[q][j] a_q = K[j][q] a_j (the
+                            // way the up-scattering half is built) it equals
+                            // K[j][q] w_j v_q - K[q][j] w_q v_j, w = u - a v = W~ (D - D^Eq)/(1 - D^Eq):
+                            // every term is proportional to the deviation from equilibrium, so FP32
+                            // rounding is relative to the net rate, not to the gross rates that are
+                            // dtau chi ~ 1e4 times larger in optically thick matter.  Each product is
+                            // formed with the same operands in the two bins it couples and
+                            // fl(e1 - e2) in bin q is exactly minus its counterpart in bin j, so NES
+                            // conserves number to the rounding of the sums.
+                            const R* w = vWdev + s * NEP;
+                            const R wq = w[q], vq = y[q];
                             for (int j = 0; j < NE; ++j) {
                                 const R kin = P0[j * LD + q], kout = P0[q * LD + j];
                                 nin = r_fma(kin, x[j], nin);        // K_In[q][j] = K_Out[j][q]
                                 nout = r_fma(kout, y[j], nout);
-                                const R e1 = __fmul_rn(kin, __fmul_rn(x[j], vq));
-                                const R e2 = __fmul_rn(kout, __fmul_rn(uq, y[j]));
+                                const R e1 = __fmul_rn(kin, __fmul_rn(w[j], vq));
+                                const R e2 = __fmul_rn(kout, __fmul_rn(wq, y[j]));
                                 cn = __fadd_rn(cn, __fsub_rn(e1, e2));
                             }
                         } else {
@@ -303,34 +319,44 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         const R* A0 = ann + (s >> 1) * NE * LD;
                         const R* x = vAW1D + pt * NEP;
                         const R* y = vWD + pt * NEP;
-                        // pair (q, j) is produced at K_Ann (p_q pbar_j), annihilated at
-                        // K_Ann (u_q ubar_j), p = a W~ (1 - D): the same products in the
-                        // particle's and the antiparticle's sums (mixed precision)
-                        const R pq = kMixed ? vAW1D[sq] : (R)0, uq = kMixed ? vWD[sq] : (R)0;
-                        const int stride_j = (s & 1) == 0 ? 1 : LD;
-                        const int base = (s & 1) == 0 ? q * LD : q;
+                        // mixed: the pair (q, j) is produced at K_Ann p_q pbar_j and annihilated at
+                        // K_Ann u_q ubar_j (p = a v); with u = w + p the net gain of either bin is
+                        // -K_Ann (w_P w_A + w_P p_A + p_P w_A) (P particle, A antiparticle),
+                        // proportional to the deviations and formed from the same operands, in
+                        // the same order, in the particle's and the antiparticle's sums
+                        const bool part = (s & 1) == 0;
+                        const R ws = kMixed ? vWdev[sq] : (R)0, ps = kMixed ? vAW1D[sq] : (R)0;
+                        const R* wpt = vWdev + pt * NEP;
+                        const int stride_j = part ? 1 : LD;
+                        const int base = part ? q * LD : q;
                         for (int j = 0; j < NE; ++j) {
                             const R av = A0[base + j * stride_j];
                             pro = r_fma(av, x[j], pro);
                             an = r_fma(av, y[j], an);
-                            if (kMixed)
-                                cp = __fadd_rn(cp, __fmul_rn(av, __fsub_rn(__fmul_rn(pq, x[j]), __fmul_rn(uq, y[j]))));
+                            if constexpr (kMixed) {
+                                const R wP = part ? ws : wpt[j], pP = part ? ps : x[j];
+                                const R wA = part ? wpt[j] : ws, pA = part ? x[j] : ps;
+                                const R tt = __fadd_rn(__fadd_rn(__fmul_rn(wP, wA), __fmul_rn(wP, pA)), __fmul_rn(pP, wA));
+                                cp = __fsub_rn(cp, __fmul_rn(av, tt));
+                            }
                         }
                         pro *= vA[sq];
                     }
                     const R eta = chiab * deq + nin + pro;          // dtau * Eq. emissivityNodal
                     const R chi = chiab + nin + nout + pro + an;    // dtau * Eq. opacityNodal
                     const R kap = chi + sig;                        // dtau * Eq. transportOpacityNodal
-                    if (kMixed) {
-                        // the same map written as Q_D = D + (D* - D + dtau C)/(1 + dtau chi), with the
-                        // net collision term dtau C = dtau (eta - chi D) built from the conservative
-                        // exchange sums; its fixed point does not depend on rounding in chi
-                        const R C = chiab * (deq - M[0]) + (cn + cp) / Wt;
+                    if constexpr (kMixed) {
+                        // the same map written as Q_D = D + W~ (D* - D + dtau C) / (W~ (1 + dtau chi)),
+                        // with the net collision term W~ dtau C = W~ dtau chi_EmAb (D^Eq - D) + net NES
+                        // + net pair exchanges.  The numerator, whose zero is the fixed point, is
+                        // summed in FP64 around the FP64 D; the denominator only scales the step, so
+                        // FP32 rounding in chi does not move the fixed point.
+                        const double numW = (double)Wt * ((Dsd - Dd) + (double)chiab * ((double)deq - Dd)) +
+                                            ((double)cn + (double)cp);
                         const R inv = (R)1 / ((R)1 + chi);
-                        Qv[0] = M[0] + (Ds - M[0] + C) * inv;
-                        // 1 - Q_D = (1 - D* + dtau (chi - eta))/(1 + dtau chi), formed from positive
-                        // terms each iteration, so the blocking factor carries no accumulated error
-                        Qv[4] = (Dsc + chiab * deqc + nout + an) * inv;
+                        dlt = (R)numW * (inv / Wt);
+                        QD = Dd + (double)dlt;
+                        Qv[0] = (R)QD;
                     } else {
                         Qv[0] = (Ds + eta) / ((R)1 + chi);          // Eq. implicitMomentsNodal, v = 0
                     }
@@ -340,16 +366,20 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                     Qv[3] = Is[2] * fI;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) F[c] = Qv[c] - M[c];
+                    if constexpr (kMixed) F[0] = dlt;
                 }
 #pragma unroll
                 for (int j = 0; j < MAXM - 1; ++j) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) { Fh[j][c] = Fh[j + 1][c]; Qh[j][c] = Qh[j + 1][c]; }
-                    if (kMixed) Qh[j][4] = Qh[j + 1][4];
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) { Fh[MAXM - 1][c] = F[c]; Qh[MAXM - 1][c] = Qv[c]; }
-                if (kMixed) Qh[MAXM - 1][4] = Qv[4];
+                if constexpr (kMixed) {
+#pragma unroll
+                    for (int j = 0; j < MAXM - 1; ++j) QhD[j] = QhD[j + 1];
+                    QhD[MAXM - 1] = QD;
+                }
                 const int m = ell < P.m_inner ? ell : P.m_inner;
                 {   // new row of the Gram matrix; least squares in FP64 (thread 0)
                     R v[MAXM];
@@ -380,28 +410,37 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                             acc = r_fma(kMixed ? (R)nd->alpha_f[j] : (R)nd->alpha[j], Qh[j][c], acc);
                     Mn[c] = act ? acc : (R)0;
                 }
-                R Dcn = Dc;
-                if (kMixed) {
-                    R acc = 0;
+                double Ddn = Dd;
+                if constexpr (kMixed) {
+                    // D in FP64 and in difference form, Q_L + sum_j alpha_j (Q_j - Q_L): the
+                    // rounding of alpha then scales only the small differences of the window
+                    double accd = QhD[MAXM - 1];
 #pragma unroll
-                    for (int j = 0; j < MAXM; ++j)
-                        if (j >= MAXM - m) acc = r_fma((R)nd->alpha_f[j], Qh[j][4], acc);
-                    Dcn = act ? acc : (R)0;
+                    for (int j = 0; j < MAXM - 1; ++j)
+                        if (j >= MAXM - m) accd = fma(nd->alpha[j], QhD[j] - QhD[MAXM - 1], accd);
+                    Ddn = act ? accd : 0.0;
+                    Mn[0] = (R)Ddn;
                 }
                 {   // Algorithm 2: per species, W-weighted squares of the change per moment
                     R v[4];
 #pragma unroll
                     for (int c = 0; c < 4; ++c) { const R d = Mn[c] - M[c]; v[c] = Wt * d * d; }
-                    if (act && !(isfinite(Mn[0]) && isfinite(Mn[1]) && isfinite(Mn[2]) && isfinite(Mn[3])))
+                    if constexpr (kMixed) { const R d = (R)(Ddn - Dd); v[0] = Wt * d * d; }
+                    if (act && !(isfinite(Mn[0]) && isfinite(Mn[1]) && isfinite(Mn[2]) && isfinite(Mn[3]) &&
+                                 isfinite(Ddn)))
                         nd->bad = 1;
                     R* out = reinterpret_cast<R*>(nd->sp_out);
                     species_sum<4, R>(v, red, out, NEP, NS);
                     if (tid == 0) {
                         int conv = 1;
+                        // mixed precision: D is an FP64 iterate and is held to tol_inner; the first
+                        // moments are FP32 values, checked against FP32 resolution at the finest
+                        const double tol_i = kMixed ? fmax(P.tol_inner, kFp32Resolution) : P.tol_inner;
                         for (int sp = 0; sp < NS; ++sp) {
-                            R mx = out[sp * 4];
-                            for (int c = 1; c < 4; ++c) mx = fmax(mx, out[sp * 4 + c]);
-                            if (!(r_sqrt(mx) <= (R)(P.tol_inner * nd->dnorm[sp]))) conv = 0;
+                            R mx = out[sp * 4 + 1];
+                            for (int c = 2; c < 4; ++c) mx = fmax(mx, out[sp * 4 + c]);
+                            if (!(r_sqrt(out[sp * 4]) <= (R)(P.tol_inner * nd->dnorm[sp]))) conv = 0;
+                            if (!(r_sqrt(mx) <= (R)(tol_i * nd->dnorm[sp]))) conv = 0;
                         }
                         nd->n_inner += 1;
                         if (nd->bad) nd->status |= NMC_NONFINITE;
@@ -412,14 +451,15 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) M[c] = Mn[c];
-                Dc = Dcn;
+                Dd = Ddn;
                 if (nd->conv_in) break;
             }
             // an inner loop stopped at its cap (or a non-finite moment) ends the node
             if (P.frozen_matter || nd->bad || (nd->status & NMC_NOT_CONVERGED_INNER)) { outer_exit = 1; }
             // ================= matter update (Eq. implicitFluidNodal), FP64 =================
             if (!outer_exit) {
-                double v[2] = {W3q * (double)M[0], gs * W2q * (double)M[0]};
+                const double Dcur = kMixed ? Dd : (double)M[0];
+                double v[2] = {W3q * Dcur, gs * W2q * Dcur};
                 block_sum<2, double>(v, red, nd->blk_out);
                 if (tid == 0) {
                     const double rho = nd->rho;
@@ -470,7 +510,8 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         }
         // ================= finalize =================
         {   // q(M, y) at the final moments (Eq. implicitFluidNodal), FP64
-            double v[2] = {W3q * (double)M[0], gs * W2q * (double)M[0]};
+            const double Dcur = kMixed ? Dd : (double)M[0];
+            double v[2] = {W3q * Dcur, gs * W2q * Dcur};
             block_sum<2, double>(v, red, nd->blk_out);
             if (tid == 0) {
                 nd->qv[0] = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * kMeVErg / nd->rho;
@@ -501,7 +542,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         }
         if (act) {
             const long long o = (n * NS + s) * NE + q;
-            a.J_out[o] = (double)M[0];
+            a.J_out[o] = kMixed ? Dd : (double)M[0];
             a.H_out[o * 3 + 0] = (double)M[1];
             a.H_out[o * 3 + 1] = (double)M[2];
             a.H_out[o * 3 + 2] = (double)M[3];
@@ -520,7 +561,7 @@ size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, bool mixed, SolveArgs* a) 
     const size_t fdq = (size_t)(mixed ? 2 : 1) * NS * ctx->n_elem * kProjQuad;
     if (fdq > mats) mats = fdq;
     const size_t b_mats = align16(mats * rs);
-    const size_t b_vec = align16((size_t)7 * NS * NEP * rs);
+    const size_t b_vec = align16((size_t)8 * NS * NEP * rs);
     const size_t b_red = align16((size_t)(threads / 32) * 8 * sizeof(double));
     const size_t b_node = align16(maxm <= 3 ? sizeof(NodeShared<3>) : sizeof(NodeShared<5>));
     if (a) {

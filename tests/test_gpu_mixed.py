@@ -1,21 +1,19 @@
-"""Mixed precision (FP32 interpolation, contractions and sweeps; FP64 conservation
-sums, matter update and least-squares solves) against the FP64 oracle.
+"""Mixed precision (FP32 interpolation, contractions and sweeps; FP64 number
+moment, conservation sums, matter update and least-squares solves) against the
+FP64 oracle.
 
 Target: <= 1e-5 relative error in D (per species, W2-weighted norm relative to
-||D_ref||), Ye, eps and T, with conservation of lepton number and energy held
-to 1e-12 relative (the matter state is formed in FP64 from the returned
-moments).  The mixed solve runs at tolerances FP32 can reach (inner 1e-6,
-outer 1e-7); the oracle runs at 1e-13.
+||D_ref||), Ye, eps and T for every species, with conservation of lepton number
+and energy held to 1e-12 relative (the matter state is formed in FP64 from the
+returned moments).  The oracle runs at 1e-13.
 
-Measured limit: for the heavy flavours (no charged-current absorption) the
-difference N_x - N_xbar is conserved by NES and pair processes and only weakly
-damped by emission/absorption, so where dtau * chi_pair >> 1 its component of
-the fixed-point residual is (1 + dtau chi) times smaller than the equation
-residual and below FP32 resolution; those spectra agree to ~1e-3 there.  The
-electron flavours, Ye, eps and T meet 1e-5 everywhere.
+The mixed solve runs at tol 1e-9 (inner and outer).  Where dtau chi ~ 1e4 the
+number-conserving NES/pair mode of the heavy flavours is damped only by
+1/(1 + dtau chi) per iteration, so Algorithm 2's change-based test leaves an
+error ~ tol (1 + dtau chi) in it (1e-3 at tol 1e-6, 5e-7 at tol 1e-9 on the
+collapse profile); reaching 1e-9 in mixed precision rests on forming the NES
+and pair exchanges from the deviation from equilibrium and on FP64 D.
 """
-
-HEAVY_BOUND = 3e-3   # heavy-flavour D where dtau chi_pair >> 1 (see module docstring)
 
 import numpy as np
 import pytest
@@ -27,7 +25,7 @@ from gpu_helpers import make_case, gpu_solve, wnorm_errors
 
 pytestmark = pytest.mark.gpu
 
-MIXED = dict(precision=nmc.MIXED, tol_inner=1e-6, tol_outer=1e-7)
+MIXED = dict(precision=nmc.MIXED, tol_inner=1e-9, tol_outer=1e-9)
 TIGHT = dict(tol_inner=1e-13, tol_outer=1e-13, max_inner=2000, max_outer=100)
 TARGET = 1e-5
 
@@ -37,11 +35,9 @@ def _check(out, ref, nodes, W2, target):
     for n, r in zip(nodes, ref):
         assert out["status"][n] == 0 and r["status"] == 0, (n, out["status"][n], r["status"])
         eD, eI = wnorm_errors(out["J"][n], out["H"][n], r["D"], r["I"], W2)
-        errs = [eD[:2].max(), eI[:2].max()] + [abs(out[k][n] - r[k]) / abs(r[k]) for k in ("Ye", "eps", "T")]
+        errs = [eD.max(), eI.max()] + [abs(out[k][n] - r[k]) / abs(r[k]) for k in ("Ye", "eps", "T")]
         worst = max(worst, max(errs))
         assert max(errs) <= target, (n, errs)
-        if len(eD) > 2:
-            assert eD[2:].max() <= HEAVY_BOUND and eI[2:].max() <= HEAVY_BOUND, (n, eD, eI)
     return worst
 
 
@@ -89,7 +85,7 @@ def test_mixed_relaxation_config():
 
 
 def test_mixed_full_size_vs_fp64_gpu():
-    """2^16 nodes: mixed against the FP64 GPU path on the same inputs, all nodes."""
+    """2^16 nodes: mixed against the FP64 GPU path (tol 1e-12) on the same inputs, all nodes and species."""
     N = 1 << 16
     edges, g, tables, inp = make_case(16, 1.875, 2, 4, "profile", N, seed=23)
     ctx = nmc.Context(edges, 2, 4, tables)
@@ -98,11 +94,7 @@ def test_mixed_full_size_vs_fp64_gpu():
     ok = (mix["status"] == 0) & (f64["status"] == 0)
     assert ok.mean() > 0.999
     eD, _ = wnorm_errors(mix["J"][ok], mix["H"][ok], f64["J"][ok], f64["H"][ok], g.W2)
-    assert eD[:, :2].max() <= TARGET, eD[:, :2].max()
-    assert eD[:, 2:].max() <= HEAVY_BOUND, eD[:, 2:].max()
-    # the heavy-flavour excess is confined to optically thick nodes
-    thin = inp["rho"][ok] < 1e12
-    assert eD[thin].max() <= TARGET
+    assert eD.max() <= TARGET, eD.max(axis=0)
     for k in ("Ye", "eps", "T"):
         assert np.max(np.abs(mix[k][ok] - f64[k][ok]) / np.abs(f64[k][ok])) <= TARGET, k
     ctx.close()
