@@ -76,7 +76,12 @@ extern "C" {
 #define NMC_MODE_FUSED 0   /* one persistent kernel: each block takes nodes from a
                               device work queue and runs Algorithm 1 on chip */
 #define NMC_MODE_PLAIN 1   /* one launch per phase and iteration over the still
-                              unconverged nodes */
+                              unconverged nodes, state in global memory, the
+                              batch in chunks of 2^17 nodes; FP64 only; the
+                              host reads list lengths back, so the call
+                              synchronises its stream and cannot be captured
+                              in a CUDA graph.  The baseline of the fused mode:
+                              same algorithm, same results. */
 
 typedef struct nmc_ctx nmc_ctx;
 
@@ -221,6 +226,15 @@ int collision_solve_noalloc(nmc_ctx* ctx, const nmc_params* params, int64_t n,
                             double* J_out, double* H_out, double* Ye_out, double* eps_out,
                             double* T_out, int32_t* n_outer, int32_t* n_inner, uint32_t* status,
                             void* stream);
+
+/*
+ * Chunk size (nodes) of NMC_MODE_PLAIN, which keeps per-node state (kernel
+ * matrices, Anderson history: ~80 KB per node at 4 species, ne = 32) in
+ * device scratch for one chunk at a time.  Default 2^17; nodes >= 1.  The
+ * scratch is allocated on the first plain call that needs it and kept until
+ * nmc_destroy.
+ */
+int nmc_set_plain_chunk(nmc_ctx* ctx, int64_t nodes);
 
 /*
  * Tetralinear table interpolation (Sec. 2.3): value of chi_EmAb (which = 0) or

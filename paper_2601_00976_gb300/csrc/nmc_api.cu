@@ -328,6 +328,8 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
 void nmc_destroy(nmc_ctx* ctx) {
     if (!ctx) return;
     for (void* p : ctx->allocations) cudaFree(p);
+    if (ctx->plain_scratch) cudaFree(ctx->plain_scratch);
+    if (ctx->plain_counts_host) cudaFreeHost(ctx->plain_counts_host);
     delete ctx;
 }
 
@@ -372,8 +374,6 @@ int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n, const dou
     if (!rho || !T_in || !Ye_in || !J_in || !H_in || !dt || !J_out || !H_out || !Ye_out || !eps_out ||
         !T_out || !n_outer || !n_inner || !status)
         return set_error(ctx, NMC_EINVAL, "null array argument");
-    if (params->mode != NMC_MODE_FUSED)
-        return set_error(ctx, NMC_EUNSUPPORTED, "plain mode is not available in this build");
     SolveArgs a{};
     a.g = ctx->g;
     a.tb = ctx->tb;
@@ -383,7 +383,15 @@ int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n, const dou
     a.J_out = J_out; a.H_out = H_out; a.Ye_out = Ye_out; a.eps_out = eps_out; a.T_out = T_out;
     a.n_outer = n_outer; a.n_inner = n_inner; a.status = status;
     a.queue = ctx->queue;
+    if (params->mode == NMC_MODE_PLAIN) return launch_plain(ctx, a, static_cast<cudaStream_t>(stream));
     return launch_fused(ctx, a, static_cast<cudaStream_t>(stream));
+}
+
+int nmc_set_plain_chunk(nmc_ctx* ctx, int64_t nodes) {
+    if (!ctx) return NMC_EINVAL;
+    if (nodes < 1 || nodes > (int64_t(1) << 30)) return set_error(ctx, NMC_EINVAL, "plain chunk must be in 1..2^30");
+    ctx->plain_chunk = nodes;
+    return NMC_OK;
 }
 
 int opacity_interp(nmc_ctx* ctx, int32_t which, int32_t species, int64_t p, const double* rho,

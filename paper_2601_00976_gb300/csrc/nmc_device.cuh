@@ -102,6 +102,65 @@ __device__ __forceinline__ void axis_cell(R v, const Axis& ax, int* i, double* t
     *t = (double)(x - (R)c);
 }
 
+// Constrained least squares of Algorithm 1 from the Gram matrix of the
+// window [base, L] (L = newest): alpha_L = 1 - sum of the others, normal
+// equations of the eliminated problem solved by Gaussian elimination with
+// partial pivoting.  Falls back to the newest map value (Picard step) when
+// the system is numerically singular.
+template <int MAXM>
+__device__ inline void anderson_solve(const double (&G)[MAXM][MAXM], int m, double* alpha) {
+    const int L = MAXM - 1, base = MAXM - m;
+    for (int j = 0; j < MAXM; ++j) alpha[j] = 0.0;
+    alpha[L] = 1.0;
+    if (m <= 1) return;
+    const int n = m - 1;
+    double A[MAXM][MAXM + 1];
+    double dmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const int gi = base + i;
+        for (int j = 0; j < n; ++j) {
+            const int gj = base + j;
+            A[i][j] = G[gi][gj] - G[gi][L] - G[gj][L] + G[L][L];
+        }
+        A[i][n] = G[L][L] - G[gi][L];
+        dmax = fmax(dmax, fabs(A[i][i]));
+    }
+    if (!(dmax > 0.0) || !isfinite(dmax)) return;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (!(fabs(A[piv][c]) > 1e-14 * dmax)) return;   // singular: Picard step
+        if (piv != c)
+            for (int j = c; j <= n; ++j) { const double t = A[c][j]; A[c][j] = A[piv][j]; A[piv][j] = t; }
+        for (int r = c + 1; r < n; ++r) {
+            const double f = A[r][c] / A[c][c];
+            for (int j = c; j <= n; ++j) A[r][j] -= f * A[c][j];
+        }
+    }
+    double gam[MAXM];
+    double sum = 0.0;
+    for (int i = n - 1; i >= 0; --i) {
+        double s = A[i][n];
+        for (int j = i + 1; j < n; ++j) s -= A[i][j] * gam[j];
+        gam[i] = s / A[i][i];
+        sum += gam[i];
+    }
+    if (!isfinite(sum)) return;
+    for (int i = 0; i < n; ++i) alpha[base + i] = gam[i];
+    alpha[L] = 1.0 - sum;
+}
+
+// Outer least squares on the 2-component scaled residuals (thread 0 only).
+__device__ inline void outer_anderson(const double (&fh)[kMaxOuterMem][2], int m, double* beta) {
+    constexpr int MM = kMaxOuterMem;
+    double G[MM][MM];
+    for (int i = 0; i < MM; ++i)
+        for (int j = 0; j < MM; ++j) G[i][j] = fh[i][0] * fh[j][0] + fh[i][1] * fh[j][1];
+    anderson_solve<MM>(G, m, beta);
+}
+
+
 // Node-wide results of the scalar part of ComputeOpacities (shared memory,
 // written by thread 0).
 struct OpacState {

@@ -137,6 +137,11 @@ struct nmc_ctx {
     // device allocations owned by the context
     std::vector<void*> allocations;
     int* queue = nullptr;
+    // plain mode: chunk size (nodes) and its scratch, grown on demand and kept
+    long long plain_chunk = 1LL << 17;
+    void* plain_scratch = nullptr;
+    size_t plain_scratch_bytes = 0;
+    int* plain_counts_host = nullptr;   // pinned
     int device = 0;
     int num_sms = 0;
     int max_smem_optin = 0;
@@ -151,6 +156,7 @@ int launch_opacity_interp(nmc_ctx* ctx, int which, int species, long long p, con
                           cudaStream_t stream);
 size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, bool mixed, SolveArgs* a);
 int launch_adjoint(nmc_ctx* ctx, AdjointArgs& a, cudaStream_t stream);
+int launch_plain(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream);
 size_t adjoint_smem_bytes(const nmc_ctx* ctx, AdjointArgs* a);
 int set_error(nmc_ctx* ctx, int code, const std::string& msg);
 }  // namespace nmc

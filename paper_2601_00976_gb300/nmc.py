@@ -57,7 +57,7 @@ class Params(ctypes.Structure):
 
 EXPORTS = ("nmc_default_params", "nmc_create", "nmc_destroy", "nmc_last_error", "nmc_energy_nodes",
            "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "collision_solve_noalloc",
-           "opacity_interp", "collision_adjoint")
+           "opacity_interp", "collision_adjoint", "nmc_set_plain_chunk")
 
 _lib = None
 
@@ -93,6 +93,8 @@ def load_library(path=LIB_PATH):
     lib.opacity_interp.restype = ctypes.c_int
     lib.collision_adjoint.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 20
     lib.collision_adjoint.restype = ctypes.c_int
+    lib.nmc_set_plain_chunk.argtypes = [vp, ctypes.c_int64]
+    lib.nmc_set_plain_chunk.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -267,6 +269,10 @@ class Context:
             self._stream_handle(stream))
         self._check(rc, "collision_adjoint")
         return out
+
+    def set_plain_chunk(self, nodes):
+        """Chunk size (nodes) of the plain per-iteration mode."""
+        self._check(self._lib.nmc_set_plain_chunk(self._h, int(nodes)), "nmc_set_plain_chunk")
 
     def opacity_interp(self, which, species, rho, T, Ye, E, out=None, stream=None):
         import torch
