@@ -228,6 +228,28 @@ int collision_solve_noalloc(nmc_ctx* ctx, const nmc_params* params, int64_t n,
                             void* stream);
 
 /*
+ * Autotuner of the fused mode.  Runs collision_solve on the given batch once
+ * per variant of the fused kernel that fits the shape: register class
+ * (__launch_bounds__ blocks per SM: 3..6 at 128 threads, 1..3 at 256) times a
+ * persistent grid of 100% or 50% of the resident capacity.  Each variant runs
+ * once untimed and once between CUDA events on `stream` (the call
+ * synchronises it).  The fastest is kept in the context for this precision,
+ * Anderson depth (m_inner <= 3 or <= 5) and block class, and later
+ * collision_solve calls with matching parameters use it; untuned keys use 4
+ * (128 threads), 2 (256) or 1 (512) blocks per SM and the full grid.
+ * Arguments as collision_solve (the outputs hold the last variant's results,
+ * identical for every variant); chosen[2] receives (blocks per SM, grid %)
+ * and *ms the winner's time (either may be NULL).  n in 1..2^30.
+ */
+int nmc_autotune(nmc_ctx* ctx, const nmc_params* params, int64_t n,
+                 const double* rho, const double* T_in, const double* Ye_in,
+                 const double* J_in, const double* H_in, const double* dt,
+                 const double* opac_scale,
+                 double* J_out, double* H_out, double* Ye_out, double* eps_out,
+                 double* T_out, int32_t* n_outer, int32_t* n_inner, uint32_t* status,
+                 int32_t* chosen, float* ms, void* stream);
+
+/*
  * Chunk size (nodes) of NMC_MODE_PLAIN, which keeps per-node state (kernel
  * matrices, Anderson history: ~80 KB per node at 4 species, ne = 32) in
  * device scratch for one chunk at a time.  Default 2^17; nodes >= 1.  The

@@ -387,6 +387,31 @@ int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n, const dou
     return launch_fused(ctx, a, static_cast<cudaStream_t>(stream));
 }
 
+int nmc_autotune(nmc_ctx* ctx, const nmc_params* params, int64_t n, const double* rho, const double* T_in,
+                 const double* Ye_in, const double* J_in, const double* H_in, const double* dt,
+                 const double* opac_scale, double* J_out, double* H_out, double* Ye_out, double* eps_out,
+                 double* T_out, int32_t* n_outer, int32_t* n_inner, uint32_t* status, int32_t* chosen,
+                 float* ms, void* stream) {
+    if (!ctx) return NMC_EINVAL;
+    int rc = nmc_check_params_internal(ctx, params);
+    if (rc != NMC_OK) return rc;
+    if (params->mode != NMC_MODE_FUSED) return set_error(ctx, NMC_EINVAL, "autotuning applies to the fused mode");
+    if (n < 1 || n > (int64_t(1) << 30)) return set_error(ctx, NMC_EINVAL, "autotune needs 1 <= n <= 2^30 nodes");
+    if (!rho || !T_in || !Ye_in || !J_in || !H_in || !dt || !J_out || !H_out || !Ye_out || !eps_out ||
+        !T_out || !n_outer || !n_inner || !status)
+        return set_error(ctx, NMC_EINVAL, "null array argument");
+    SolveArgs a{};
+    a.g = ctx->g;
+    a.tb = ctx->tb;
+    a.p = *params;
+    a.n = n;
+    a.rho = rho; a.T = T_in; a.Ye = Ye_in; a.J = J_in; a.H = H_in; a.dt = dt; a.scale = opac_scale;
+    a.J_out = J_out; a.H_out = H_out; a.Ye_out = Ye_out; a.eps_out = eps_out; a.T_out = T_out;
+    a.n_outer = n_outer; a.n_inner = n_inner; a.status = status;
+    a.queue = ctx->queue;
+    return autotune_fused(ctx, a, static_cast<cudaStream_t>(stream), chosen, ms);
+}
+
 int nmc_set_plain_chunk(nmc_ctx* ctx, int64_t nodes) {
     if (!ctx) return NMC_EINVAL;
     if (nodes < 1 || nodes > (int64_t(1) << 30)) return set_error(ctx, NMC_EINVAL, "plain chunk must be in 1..2^30");

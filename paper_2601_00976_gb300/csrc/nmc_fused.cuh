@@ -1,0 +1,548 @@
+// Fused, persistent kernel for the implicit neutrino--matter collision solve
+// (Sec. 3.5, Algorithm 1 with Algorithms 2 and 3), in two precisions:
+//   R = double  every step in FP64;
+//   R = float   mixed: table interpolation, D^Eq, kernel contractions and the
+//               fixed-point sweeps (map Q, residuals, Anderson mixing, Gram
+//               sums, Algorithm 2) in FP32; conservation sums, matter update,
+//               the Anderson least-squares solves and the final EoS step in FP64.
+//
+// Mapping.  One thread block solves one spatial node at a time; blocks are
+// persistent and take node indices from a device work queue (an atomic
+// counter), so nodes with many iterations do not hold up others.  Inside a
+// block, thread (s, q) owns species s at energy node q: its moments
+// (D, I^1, I^2, I^3), old moments, opacities and its slice of the Anderson
+// history (registers).  The node's NES kernels Phi_Out[s] (one ne x ne matrix
+// per species) and pair kernels Phi_Ann[p] (one per particle/antiparticle
+// pair) live in shared memory, rows padded to ne + 1 so that both row- and
+// column-wise reads are free of bank conflicts.
+//
+// Scaling.  Rates are formed as dimensionless products: matrices hold
+// K = dtau * (4 pi / (hc)^3) * Phi and vectors hold W~ D with
+// W~_q = w_q eps_q^2 Delta eps_e = W2_q / (4 pi / (hc)^3), so that
+// sum_q' K W~ D = dtau * (rate of Eqs. nesRatesNodal / pairRatesNodal);
+// chi_EmAb and sigma_Iso are carried as dtau * chi.  Every intermediate is
+// O(1e-30 .. 1e8), inside FP32 range.
+//
+// Per outer iteration (ComputeOpacities of Alg. 1): EoS -> chemical
+// potentials; Fermi--Dirac values at the projection quadrature points (all
+// threads), eps^2-weighted projection and bound limiter per (species, element)
+// (Eq. fermiDiracProjection); trilinear log-table interpolation of chi_EmAb and
+// sigma_Iso with coalesced rows of ne energies; bilinear (log10 T, eta)
+// interpolation of the kernel tables into shared memory, then the NES
+// up-scattering triangle by detailed balance (Eqs. inOutInvarianceNES,
+// detailedBalanceNES).
+//
+// Per inner iteration: rates as shared-memory mat-vecs (Phi_In = Phi_Out^T;
+// the antiparticle's Phi_Ann is the transpose; Phi_Pro = a_s(q) a_sbar(q')
+// Phi_Ann with a = D/(1-D) by Eq. detailedBalancePair), the map Q
+// (Eq. implicitMomentsNodal, v = 0), one block reduction for the new row of the
+// Anderson Gram matrix, the least-squares solve in thread 0 (FP64), the mixing
+// update, and a per-species reduction for Algorithm 2.
+//
+// Matter update (Eq. implicitFluidNodal with Eqs. eulerianEnergyLG,
+// eulerianNumberLG): one FP64 block reduction for E_nu and N_nu, the outer
+// Anderson step and Algorithm 3 in thread 0, then T by EoS root finding.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <math.h>
+
+#include "nmc_internal.h"
+#include "nmc_eos.cuh"
+#include "nmc_device.cuh"
+
+namespace nmc {
+
+namespace {
+
+// Finest relative change of an FP32 moment the mixed path checks (4 ulp of 1).
+constexpr double kFp32Resolution = 4.0 * 1.1920928955078125e-7;
+
+template <int MAXM>
+struct NodeShared {
+    double rho, dtau, T;
+    double sc[4];
+    double y[2], ystar[2], qv[2];
+    double EN_star[2];
+    double qh[kMaxOuterMem][2], fh[kMaxOuterMem][2];
+    double G[MAXM][MAXM];
+    double alpha[MAXM];
+    float alpha_f[MAXM];
+    double dnorm[kMaxSpecies];
+    double sp_out[kMaxSpecies * 4];
+    double blk_out[8];
+    OpacState op;
+    long long node;
+    int status, n_inner, n_outer;
+    int conv_in, conv_out, bad, done;
+};
+
+}  // namespace
+
+// MAXT: block-size class (threads = ns * nep rounded up to 32 must not exceed
+// it); MINB blocks per SM cap registers at 128 per thread in every class.
+template <typename R, int MAXM, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
+    constexpr bool kMixed = sizeof(R) == 4;
+    extern __shared__ __align__(16) unsigned char smb[];
+    const DevGrid& g = a.g;
+    const int NS = g.ns, NE = g.ne, NEP = g.nep, LD = g.ld;
+    const int tid = threadIdx.x;
+    const int s = tid / NEP, q = tid - s * NEP;
+    const bool act = (s < NS) && (q < NE);
+    const int sq = s * NEP + q;
+
+    R* phi = reinterpret_cast<R*>(smb + a.off_phi);   // [NS][NE][LD]   K_Out per species
+    R* ann = reinterpret_cast<R*>(smb + a.off_ann);   // [NS/2][NE][LD] K_Ann per pair (particle)
+    R* vWD = reinterpret_cast<R*>(smb + a.off_vec);   // [NS][NEP] W~ D
+    R* vW1D = vWD + NS * NEP;                          //           W~ (1 - D)
+    R* vAW1D = vW1D + NS * NEP;                        //           a W~ (1 - D)
+    R* vA = vAW1D + NS * NEP;                          //           a = D^Eq / (1 - D^Eq)
+    R* vAi = vA + NS * NEP;                            //           1 / a
+    R* vDeq = vAi + NS * NEP;                          //           D^Eq
+    R* vDeqc = vDeq + NS * NEP;                        //           1 - D^Eq (mixed)
+    R* vWdev = vDeqc + NS * NEP;                        //           w = W~ (D - D^Eq) / (1 - D^Eq) (mixed)
+    void* red = smb + a.off_red;                       // reduction scratch
+    NodeShared<MAXM>* nd = reinterpret_cast<NodeShared<MAXM>*>(smb + a.off_node);
+    const OpacBufs<R> ob{phi, ann, vA, vAi, vDeq, vDeqc};
+
+    const nmc_params& P = a.p;
+    const bool nes_on = (P.proc_mask & NMC_PROC_NES) != 0;
+    const bool pair_on = (P.proc_mask & NMC_PROC_PAIR) != 0;
+    const double gs = (s == 0) ? 1.0 : (s == 1 ? -1.0 : 0.0);
+    const double W2q = act ? g.w2[q] : 0.0;
+    const double W3q = act ? g.w3[q] : 0.0;
+    const R Wt = act ? (kMixed ? (R)g.wt_f[q] : (R)g.wt[q]) : (R)0;
+
+    // Mixed precision keeps the number moment D and its map values in FP64
+    // (QhD): near a fixed point where 1 + dtau chi ~ 1e4, FP32 increments of D
+    // fall below one ulp long before the equation residual is small.
+    R Fh[MAXM][4], Qh[MAXM][4];
+    double QhD[kMixed ? MAXM : 1];
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Fh[j][c] = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Qh[j][c] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < (kMixed ? MAXM : 1); ++j) QhD[j] = 0.0;
+
+    for (;;) {
+        if (tid == 0) nd->node = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const long long n = nd->node;
+        if (n >= a.n) break;
+
+        // ---------------- node set-up ----------------
+        double Dsd = 0.0, Isd[3] = {0.0, 0.0, 0.0};
+        if (act) {
+            const long long o = (n * NS + s) * NE + q;
+            Dsd = a.J[o];
+            Isd[0] = a.H[o * 3 + 0];
+            Isd[1] = a.H[o * 3 + 1];
+            Isd[2] = a.H[o * 3 + 2];
+        }
+        if (tid == 0) {
+            const double rho = a.rho[n], T = a.T[n], Ye = a.Ye[n], dt = a.dt[n];
+            nd->rho = rho;
+            nd->T = T;
+            nd->dtau = kC * dt;
+            for (int k = 0; k < 4; ++k) nd->sc[k] = a.scale ? a.scale[n * 4 + k] : 1.0;
+            const bool okin = rho > 0.0 && isfinite(rho) && T > 0.0 && isfinite(T) &&
+                              Ye > 0.0 && Ye < 1.0 && dt >= 0.0 && isfinite(dt);
+            nd->status = okin ? 0 : NMC_BAD_INPUT;
+            double e = 0.0, de = 0.0;
+            if (okin) eos_eps(rho, T, Ye, &e, &de);
+            nd->ystar[0] = e;
+            nd->ystar[1] = Ye;
+            nd->y[0] = e;
+            nd->y[1] = Ye;
+            nd->n_inner = 0;
+            nd->n_outer = 0;
+            nd->bad = 0;
+            nd->done = okin ? 0 : 1;
+        }
+        __syncthreads();
+        if (nd->done) {   // invalid input: outputs = inputs
+            if (act) {
+                const long long o = (n * NS + s) * NE + q;
+                a.J_out[o] = Dsd;
+                for (int j = 0; j < 3; ++j) a.H_out[o * 3 + j] = Isd[j];
+            }
+            if (tid == 0) {
+                a.Ye_out[n] = a.Ye[n];
+                a.eps_out[n] = nd->ystar[0];
+                a.T_out[n] = a.T[n];
+                a.n_outer[n] = 0;
+                a.n_inner[n] = 0;
+                a.status[n] = nd->status;
+            }
+            __syncthreads();
+            continue;
+        }
+        {   // E_nu*, N_nu* in FP64 (Eqs. eulerianEnergyLG, eulerianNumberLG at v = 0)
+            double v[2] = {W3q * Dsd, gs * W2q * Dsd};
+            block_sum<2, double>(v, red, nd->blk_out);
+            if (tid == 0) { nd->EN_star[0] = nd->blk_out[0]; nd->EN_star[1] = nd->blk_out[1]; }
+        }
+        const R Ds = (R)Dsd;
+        const R Is[3] = {(R)Isd[0], (R)Isd[1], (R)Isd[2]};
+        R M[4] = {Ds, Is[0], Is[1], Is[2]};
+        double Dd = Dsd;   // FP64 number moment (mixed precision); M[0] is its FP32 shadow
+        R chiab = 0, sig = 0, deq = 0, deqc = 0;
+        int outer_exit = 0;
+
+        for (int k = 1;; ++k) {
+            // ================= ComputeOpacities(y^[k]) =================
+            compute_opacities<R>(g, a.tb, P, nd->rho, nd->T, nd->y[1], nd->dtau, nd->sc, ob, &nd->op,
+                                 &nd->status, chiab, sig, deq, deqc);
+            // reference norm ||D^[k,1]||_W per species (Algorithm 2 input)
+            {
+                R v[1] = {Wt * M[0] * M[0]};
+                R* out = reinterpret_cast<R*>(nd->sp_out);
+                species_sum<1, R>(v, red, out, NEP, NS);
+                if (tid == 0) {
+                    const double fl = P.norm_floor * sqrt(g.sum_wt);
+                    for (int sp = 0; sp < NS; ++sp) nd->dnorm[sp] = fmax((double)r_sqrt(out[sp]), fl);
+                }
+            }
+            // ================= inner loop =================
+            for (int ell = 1;; ++ell) {
+                if (act) {
+                    // mixed: the blocking factor 1 - D and the deviation D - D^Eq are formed from
+                    // the FP64 D (1 - D in FP32 has no digits left at D ~ 1 - 1e-6)
+                    const R hole = kMixed ? (R)(1.0 - Dd) : (R)1 - M[0];
+                    vWD[sq] = Wt * M[0];
+                    vW1D[sq] = Wt * hole;
+                    vAW1D[sq] = vA[sq] * Wt * hole;
+                    if constexpr (kMixed) vWdev[sq] = (R)(Dd - (double)deq) * (Wt / deqc);
+                }
+                __syncthreads();
+                R F[4] = {0, 0, 0, 0}, Qv[4] = {0, 0, 0, 0};
+                double QD = 0.0;   // mixed: Q_D in FP64
+                R dlt = 0;         // mixed: Q_D - D, formed without cancellation
+                if (act) {
+                    R nin = 0, nout = 0, pro = 0, an = 0;
+                    R cn = 0, cp = 0;   // mixed: net NES / pair exchange terms (deviation form)
+                    if (nes_on) {
+                        const R* P0 = phi + s * NE * LD;
+                        const R* x = vWD + s * NEP;
+                        const R* y = vW1D + s * NEP;
+                        if constexpr (kMixed) {
+                            // Net exchange with bin j: K[j][q] u_j v_q - K[q][j] u_q v_j, u = W~ D,
+                            // v = W~ (1 - D).  With detailed balance K[q][j] a_q = K[j][q] a_j (the
+                            // way the up-scattering half is built) it equals
+                            // K[j][q] w_j v_q - K[q][j] w_q v_j, w = u - a v = W~ (D - D^Eq)/(1 - D^Eq):
+                            // every term is proportional to the deviation from equilibrium, so FP32
+                            // rounding is relative to the net rate, not to the gross rates that are
+                            // dtau chi ~ 1e4 times larger in optically thick matter.  Each product is
+                            // formed with the same operands in the two bins it couples and
+                            // fl(e1 - e2) in bin q is exactly minus its counterpart in bin j, so NES
+                            // conserves number to the rounding of the sums.
+                            const R* w = vWdev + s * NEP;
+                            const R wq = w[q], vq = y[q];
+                            for (int j = 0; j < NE; ++j) {
+                                const R kin = P0[j * LD + q], kout = P0[q * LD + j];
+                                nin = r_fma(kin, x[j], nin);        // K_In[q][j] = K_Out[j][q]
+                                nout = r_fma(kout, y[j], nout);
+                                const R e1 = __fmul_rn(kin, __fmul_rn(w[j], vq));
+                                const R e2 = __fmul_rn(kout, __fmul_rn(wq, y[j]));
+                                cn = __fadd_rn(cn, __fsub_rn(e1, e2));
+                            }
+                        } else {
+                            for (int j = 0; j < NE; ++j) {
+                                nin = r_fma(P0[j * LD + q], x[j], nin);    // K_In[q][j] = K_Out[j][q]
+                                nout = r_fma(P0[q * LD + j], y[j], nout);
+                            }
+                        }
+                    }
+                    if (pair_on) {
+                        const int pt = s ^ 1;
+                        const R* A0 = ann + (s >> 1) * NE * LD;
+                        const R* x = vAW1D + pt * NEP;
+                        const R* y = vWD + pt * NEP;
+                        // mixed: the pair (q, j) is produced at K_Ann p_q pbar_j and annihilated at
+                        // K_Ann u_q ubar_j (p = a v); with u = w + p the net gain of either bin is
+                        // -K_Ann (w_P w_A + w_P p_A + p_P w_A) (P particle, A antiparticle),
+                        // proportional to the deviations and formed from the same operands, in
+                        // the same order, in the particle's and the antiparticle's sums
+                        const bool part = (s & 1) == 0;
+                        const R ws = kMixed ? vWdev[sq] : (R)0, ps = kMixed ? vAW1D[sq] : (R)0;
+                        const R* wpt = vWdev + pt * NEP;
+                        const int stride_j = part ? 1 : LD;
+                        const int base = part ? q * LD : q;
+                        for (int j = 0; j < NE; ++j) {
+                            const R av = A0[base + j * stride_j];
+                            pro = r_fma(av, x[j], pro);
+                            an = r_fma(av, y[j], an);
+                            if constexpr (kMixed) {
+                                const R wP = part ? ws : wpt[j], pP = part ? ps : x[j];
+                                const R wA = part ? wpt[j] : ws, pA = part ? x[j] : ps;
+                                const R tt = __fadd_rn(__fadd_rn(__fmul_rn(wP, wA), __fmul_rn(wP, pA)), __fmul_rn(pP, wA));
+                                cp = __fsub_rn(cp, __fmul_rn(av, tt));
+                            }
+                        }
+                        pro *= vA[sq];
+                    }
+                    const R eta = chiab * deq + nin + pro;          // dtau * Eq. emissivityNodal
+                    const R chi = chiab + nin + nout + pro + an;    // dtau * Eq. opacityNodal
+                    const R kap = chi + sig;                        // dtau * Eq. transportOpacityNodal
+                    if constexpr (kMixed) {
+                        // the same map written as Q_D = D + W~ (D* - D + dtau C) / (W~ (1 + dtau chi)),
+                        // with the net collision term W~ dtau C = W~ dtau chi_EmAb (D^Eq - D) + net NES
+                        // + net pair exchanges.  The numerator, whose zero is the fixed point, is
+                        // summed in FP64 around the FP64 D; the denominator only scales the step, so
+                        // FP32 rounding in chi does not move the fixed point.
+                        const double numW = (double)Wt * ((Dsd - Dd) + (double)chiab * ((double)deq - Dd)) +
+                                            ((double)cn + (double)cp);
+                        const R inv = (R)1 / ((R)1 + chi);
+                        dlt = (R)numW * (inv / Wt);
+                        QD = Dd + (double)dlt;
+                        Qv[0] = (R)QD;
+                    } else {
+                        Qv[0] = (Ds + eta) / ((R)1 + chi);          // Eq. implicitMomentsNodal, v = 0
+                    }
+                    const R fI = (R)1 / ((R)1 + kap);
+                    Qv[1] = Is[0] * fI;
+                    Qv[2] = Is[1] * fI;
+                    Qv[3] = Is[2] * fI;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) F[c] = Qv[c] - M[c];
+                    if constexpr (kMixed) F[0] = dlt;
+                }
+#pragma unroll
+                for (int j = 0; j < MAXM - 1; ++j) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) { Fh[j][c] = Fh[j + 1][c]; Qh[j][c] = Qh[j + 1][c]; }
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) { Fh[MAXM - 1][c] = F[c]; Qh[MAXM - 1][c] = Qv[c]; }
+                if constexpr (kMixed) {
+#pragma unroll
+                    for (int j = 0; j < MAXM - 1; ++j) QhD[j] = QhD[j + 1];
+                    QhD[MAXM - 1] = QD;
+                }
+                const int m = ell < P.m_inner ? ell : P.m_inner;
+                {   // new row of the Gram matrix; least squares in FP64 (thread 0)
+                    R v[MAXM];
+#pragma unroll
+                    for (int j = 0; j < MAXM; ++j)
+                        v[j] = F[0] * Fh[j][0] + F[1] * Fh[j][1] + F[2] * Fh[j][2] + F[3] * Fh[j][3];
+                    R* out = reinterpret_cast<R*>(nd->blk_out);
+                    block_sum<MAXM, R>(v, red, out);
+                    if (tid == 0) {
+                        for (int i = 0; i < MAXM - 1; ++i)
+                            for (int j = 0; j < MAXM - 1; ++j) nd->G[i][j] = nd->G[i + 1][j + 1];
+                        for (int j = 0; j < MAXM; ++j) {
+                            nd->G[MAXM - 1][j] = (double)out[j];
+                            nd->G[j][MAXM - 1] = (double)out[j];
+                        }
+                        anderson_solve<MAXM>(nd->G, m, nd->alpha);
+                        for (int j = 0; j < MAXM; ++j) nd->alpha_f[j] = (float)nd->alpha[j];
+                    }
+                    __syncthreads();
+                }
+                R Mn[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    R acc = 0;
+#pragma unroll
+                    for (int j = 0; j < MAXM; ++j)
+                        if (j >= MAXM - m)   // window only
+                            acc = r_fma(kMixed ? (R)nd->alpha_f[j] : (R)nd->alpha[j], Qh[j][c], acc);
+                    Mn[c] = act ? acc : (R)0;
+                }
+                double Ddn = Dd;
+                if constexpr (kMixed) {
+                    // D in FP64 and in difference form, Q_L + sum_j alpha_j (Q_j - Q_L): the
+                    // rounding of alpha then scales only the small differences of the window
+                    double accd = QhD[MAXM - 1];
+#pragma unroll
+                    for (int j = 0; j < MAXM - 1; ++j)
+                        if (j >= MAXM - m) accd = fma(nd->alpha[j], QhD[j] - QhD[MAXM - 1], accd);
+                    Ddn = act ? accd : 0.0;
+                    Mn[0] = (R)Ddn;
+                }
+                {   // Algorithm 2: per species, W-weighted squares of the change per moment
+                    R v[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) { const R d = Mn[c] - M[c]; v[c] = Wt * d * d; }
+                    if constexpr (kMixed) { const R d = (R)(Ddn - Dd); v[0] = Wt * d * d; }
+                    if (act && !(isfinite(Mn[0]) && isfinite(Mn[1]) && isfinite(Mn[2]) && isfinite(Mn[3]) &&
+                                 isfinite(Ddn)))
+                        nd->bad = 1;
+                    R* out = reinterpret_cast<R*>(nd->sp_out);
+                    species_sum<4, R>(v, red, out, NEP, NS);
+                    if (tid == 0) {
+                        int conv = 1;
+                        // mixed precision: D is an FP64 iterate and is held to tol_inner; the first
+                        // moments are FP32 values, checked against FP32 resolution at the finest
+                        const double tol_i = kMixed ? fmax(P.tol_inner, kFp32Resolution) : P.tol_inner;
+                        for (int sp = 0; sp < NS; ++sp) {
+                            R mx = out[sp * 4 + 1];
+                            for (int c = 2; c < 4; ++c) mx = fmax(mx, out[sp * 4 + c]);
+                            if (!(r_sqrt(out[sp * 4]) <= (R)(P.tol_inner * nd->dnorm[sp]))) conv = 0;
+                            if (!(r_sqrt(mx) <= (R)(tol_i * nd->dnorm[sp]))) conv = 0;
+                        }
+                        nd->n_inner += 1;
+                        if (nd->bad) nd->status |= NMC_NONFINITE;
+                        if (!conv && !nd->bad && ell >= P.max_inner) nd->status |= NMC_NOT_CONVERGED_INNER;
+                        nd->conv_in = conv || nd->bad || ell >= P.max_inner;
+                    }
+                    __syncthreads();
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) M[c] = Mn[c];
+                Dd = Ddn;
+                if (nd->conv_in) break;
+            }
+            // an inner loop stopped at its cap (or a non-finite moment) ends the node
+            if (P.frozen_matter || nd->bad || (nd->status & NMC_NOT_CONVERGED_INNER)) { outer_exit = 1; }
+            // ================= matter update (Eq. implicitFluidNodal), FP64 =================
+            if (!outer_exit) {
+                const double Dcur = kMixed ? Dd : (double)M[0];
+                double v[2] = {W3q * Dcur, gs * W2q * Dcur};
+                block_sum<2, double>(v, red, nd->blk_out);
+                if (tid == 0) {
+                    const double rho = nd->rho;
+                    const double qv0 = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * kMeVErg / rho;
+                    const double qv1 = nd->ystar[1] - kMB * (nd->blk_out[1] - nd->EN_star[1]) / rho;
+                    nd->qv[0] = qv0;
+                    nd->qv[1] = qv1;
+                    // outer Anderson on residuals scaled by |y*|
+                    for (int j = 0; j < kMaxOuterMem - 1; ++j) {
+                        nd->qh[j][0] = nd->qh[j + 1][0]; nd->qh[j][1] = nd->qh[j + 1][1];
+                        nd->fh[j][0] = nd->fh[j + 1][0]; nd->fh[j][1] = nd->fh[j + 1][1];
+                    }
+                    nd->qh[kMaxOuterMem - 1][0] = qv0;
+                    nd->qh[kMaxOuterMem - 1][1] = qv1;
+                    nd->fh[kMaxOuterMem - 1][0] = (qv0 - nd->y[0]) / fabs(nd->ystar[0]);
+                    nd->fh[kMaxOuterMem - 1][1] = (qv1 - nd->y[1]) / fabs(nd->ystar[1]);
+                    const int mo = k < P.m_outer ? k : P.m_outer;
+                    double beta[kMaxOuterMem];
+                    outer_anderson(nd->fh, mo, beta);
+                    double yn0 = 0.0, yn1 = 0.0;
+                    for (int j = kMaxOuterMem - mo; j < kMaxOuterMem; ++j) {
+                        yn0 += beta[j] * nd->qh[j][0];
+                        yn1 += beta[j] * nd->qh[j][1];
+                    }
+                    const int conv = fabs(yn0 - nd->y[0]) <= P.tol_outer * fabs(nd->ystar[0]) &&
+                                     fabs(yn1 - nd->y[1]) <= P.tol_outer * fabs(nd->ystar[1]);   // Algorithm 3
+                    nd->y[0] = yn0;
+                    nd->y[1] = yn1;
+                    int stop = conv;
+                    if (!(isfinite(yn0) && isfinite(yn1))) { nd->status |= NMC_NONFINITE; stop = 1; }
+                    if (!stop && k >= P.max_outer) { nd->status |= NMC_NOT_CONVERGED_OUTER; stop = 1; }
+                    if (!stop) {   // an iterate outside the EoS domain stops the node
+                        bool ok;
+                        const double Tn = kMixed ? eos_temperature_mixed(rho, yn0, yn1, nd->T, &ok)
+                                                 : eos_temperature(rho, yn0, yn1, nd->T, &ok);
+                        if (ok) nd->T = Tn;
+                        else { nd->status |= NMC_EOS_FAIL; stop = 1; }
+                    }
+                    nd->conv_out = stop;
+                }
+                __syncthreads();
+                if (nd->conv_out) outer_exit = 1;
+            }
+            if (outer_exit) {
+                if (tid == 0) nd->n_outer = k;
+                break;
+            }
+        }
+        // ================= finalize =================
+        {   // q(M, y) at the final moments (Eq. implicitFluidNodal), FP64
+            const double Dcur = kMixed ? Dd : (double)M[0];
+            double v[2] = {W3q * Dcur, gs * W2q * Dcur};
+            block_sum<2, double>(v, red, nd->blk_out);
+            if (tid == 0) {
+                nd->qv[0] = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * kMeVErg / nd->rho;
+                nd->qv[1] = nd->ystar[1] - kMB * (nd->blk_out[1] - nd->EN_star[1]) / nd->rho;
+            }
+        }
+        if (tid == 0) {
+            const double rho = nd->rho;
+            double yo0, yo1, To;
+            if (P.frozen_matter) {
+                yo0 = nd->ystar[0]; yo1 = nd->ystar[1]; To = a.T[n];
+            } else if (nd->status & NMC_NONFINITE) {
+                yo0 = nd->y[0]; yo1 = nd->y[1]; To = nd->T;
+            } else {
+                if (P.final_q) { yo0 = nd->qv[0]; yo1 = nd->qv[1]; }   // y = q(M, y) at converged M
+                else { yo0 = nd->y[0]; yo1 = nd->y[1]; }                // Anderson-mixed iterate
+                bool ok;
+                To = kMixed ? eos_temperature_mixed(rho, yo0, yo1, nd->T, &ok)
+                            : eos_temperature(rho, yo0, yo1, nd->T, &ok);
+                if (!ok) { nd->status |= NMC_EOS_FAIL; To = nd->T; }   // last T inside the domain
+            }
+            a.Ye_out[n] = yo1;
+            a.eps_out[n] = yo0;
+            a.T_out[n] = To;
+            a.n_outer[n] = nd->n_outer;
+            a.n_inner[n] = nd->n_inner;
+            a.status[n] = (uint32_t)nd->status;
+        }
+        if (act) {
+            const long long o = (n * NS + s) * NE + q;
+            a.J_out[o] = kMixed ? Dd : (double)M[0];
+            a.H_out[o * 3 + 0] = (double)M[1];
+            a.H_out[o * 3 + 1] = (double)M[2];
+            a.H_out[o * 3 + 2] = (double)M[3];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename R, int MAXM, int MAXT, int MINB>
+static int launch_impl(nmc_ctx* ctx, SolveArgs a, cudaStream_t stream, int grid_pct) {
+    auto kern = fused_kernel<R, MAXM, MAXT, MINB>;
+    const size_t smem = fused_smem_bytes(ctx, MAXM, sizeof(R) == 4, &a);
+    if ((int)smem > ctx->max_smem_optin)
+        return set_error(ctx, NMC_EUNSUPPORTED, "shared-memory footprint of the fused kernel exceeds the per-block limit");
+    const int threads = ((ctx->ns * ctx->nep + 31) / 32) * 32;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return set_error(ctx, NMC_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (e != cudaSuccess || per_sm < 1)
+        return set_error(ctx, NMC_EUNSUPPORTED, "fused kernel cannot be resident with this shape");
+    long long grid = (long long)per_sm * ctx->num_sms * grid_pct / 100;
+    if (grid < ctx->num_sms) grid = ctx->num_sms;
+    if (grid > a.n) grid = a.n;
+    e = cudaMemsetAsync(a.queue, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return set_error(ctx, NMC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    kern<<<(unsigned)grid, threads, smem, stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(ctx, NMC_ECUDA, std::string("fused kernel launch: ") + cudaGetErrorString(e));
+    return NMC_OK;
+}
+
+// Kernel variant v: register class (blocks per SM the registers must allow) and
+// persistent grid size.  Block-size classes follow the shape: threads =
+// ns * nep rounded up to 32 must not exceed MAXT.
+template <typename R, int MAXM>
+static int launch_by_variant(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v) {
+    const int threads = ((ctx->ns * ctx->nep + 31) / 32) * 32;
+    if (threads <= 128) {
+        switch (v.minb) {
+            case 3: return launch_impl<R, MAXM, 128, 3>(ctx, a, stream, v.grid_pct);
+            case 5: return launch_impl<R, MAXM, 128, 5>(ctx, a, stream, v.grid_pct);
+            case 6: return launch_impl<R, MAXM, 128, 6>(ctx, a, stream, v.grid_pct);
+            default: return launch_impl<R, MAXM, 128, 4>(ctx, a, stream, v.grid_pct);
+        }
+    }
+    if (threads <= 256) {
+        switch (v.minb) {
+            case 1: return launch_impl<R, MAXM, 256, 1>(ctx, a, stream, v.grid_pct);
+            case 3: return launch_impl<R, MAXM, 256, 3>(ctx, a, stream, v.grid_pct);
+            default: return launch_impl<R, MAXM, 256, 2>(ctx, a, stream, v.grid_pct);
+        }
+    }
+    return launch_impl<R, MAXM, 512, 1>(ctx, a, stream, v.grid_pct);
+}
+
+}  // namespace nmc

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -96,6 +97,14 @@ struct SolveArgs {
     int off_phi, off_ann, off_vec, off_red, off_node;
 };
 
+// A variant of the fused kernel: the register class (blocks per SM its
+// registers must allow, __launch_bounds__) and the persistent grid as a
+// percentage of the resident capacity.
+struct FusedVariant {
+    int minb;
+    int grid_pct;
+};
+
 // Arguments of the adjoint kernel (collision_adjoint).
 struct AdjointArgs {
     DevGrid g;
@@ -142,6 +151,8 @@ struct nmc_ctx {
     void* plain_scratch = nullptr;
     size_t plain_scratch_bytes = 0;
     int* plain_counts_host = nullptr;   // pinned
+    // autotuned fused-kernel variants, keyed by precision, Anderson depth and block class
+    std::map<int, nmc::FusedVariant> tuned;
     int device = 0;
     int num_sms = 0;
     int max_smem_optin = 0;
@@ -157,6 +168,11 @@ int launch_opacity_interp(nmc_ctx* ctx, int which, int species, long long p, con
 size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, bool mixed, SolveArgs* a);
 int launch_adjoint(nmc_ctx* ctx, AdjointArgs& a, cudaStream_t stream);
 int launch_plain(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream);
+int launch_fused_f64_m3(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
+int launch_fused_f64_m5(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
+int launch_fused_f32_m3(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
+int launch_fused_f32_m5(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
+int autotune_fused(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, int32_t* chosen, float* chosen_ms);
 size_t adjoint_smem_bytes(const nmc_ctx* ctx, AdjointArgs* a);
 int set_error(nmc_ctx* ctx, int code, const std::string& msg);
 }  // namespace nmc

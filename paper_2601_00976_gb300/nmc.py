@@ -57,7 +57,7 @@ class Params(ctypes.Structure):
 
 EXPORTS = ("nmc_default_params", "nmc_create", "nmc_destroy", "nmc_last_error", "nmc_energy_nodes",
            "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "collision_solve_noalloc",
-           "opacity_interp", "collision_adjoint", "nmc_set_plain_chunk")
+           "opacity_interp", "collision_adjoint", "nmc_set_plain_chunk", "nmc_autotune")
 
 _lib = None
 
@@ -93,6 +93,8 @@ def load_library(path=LIB_PATH):
     lib.opacity_interp.restype = ctypes.c_int
     lib.collision_adjoint.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 20
     lib.collision_adjoint.restype = ctypes.c_int
+    lib.nmc_autotune.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 18
+    lib.nmc_autotune.restype = ctypes.c_int
     lib.nmc_set_plain_chunk.argtypes = [vp, ctypes.c_int64]
     lib.nmc_set_plain_chunk.restype = ctypes.c_int
     _lib = lib
@@ -269,6 +271,30 @@ class Context:
             self._stream_handle(stream))
         self._check(rc, "collision_adjoint")
         return out
+
+    def autotune(self, params, rho, T, Ye, J, H, dt, scale=None, stream=None):
+        """Time the fused kernel's variants on this batch and keep the fastest for these parameters.
+
+        Returns (blocks_per_sm, grid_percent, milliseconds) of the chosen variant.
+        """
+        import torch
+        n = rho.shape[0]
+        f64 = dict(dtype=torch.float64, device=rho.device)
+        out = dict(J=torch.empty_like(J), H=torch.empty_like(H), Ye=torch.empty(n, **f64),
+                   eps=torch.empty(n, **f64), T=torch.empty(n, **f64),
+                   n_outer=torch.empty(n, dtype=torch.int32, device=rho.device),
+                   n_inner=torch.empty(n, dtype=torch.int32, device=rho.device),
+                   status=torch.empty(n, dtype=torch.int32, device=rho.device))
+        chosen = (ctypes.c_int32 * 2)()
+        ms = ctypes.c_float()
+        p = lambda x: ctypes.c_void_p(x.data_ptr()) if x is not None else None  # noqa: E731
+        rc = self._lib.nmc_autotune(
+            self._h, ctypes.byref(params), n, p(rho), p(T), p(Ye), p(J), p(H), p(dt), p(scale),
+            p(out["J"]), p(out["H"]), p(out["Ye"]), p(out["eps"]), p(out["T"]),
+            p(out["n_outer"]), p(out["n_inner"]), p(out["status"]), ctypes.cast(chosen, ctypes.c_void_p),
+            ctypes.cast(ctypes.pointer(ms), ctypes.c_void_p), self._stream_handle(stream))
+        self._check(rc, "nmc_autotune")
+        return int(chosen[0]), int(chosen[1]), float(ms.value)
 
     def set_plain_chunk(self, nodes):
         """Chunk size (nodes) of the plain per-iteration mode."""

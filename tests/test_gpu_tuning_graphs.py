@@ -1,0 +1,71 @@
+"""Autotuned variants of the fused kernel and CUDA-graph capture of collision_solve.
+
+A variant changes only the register budget and the size of the persistent
+grid: the per-node arithmetic is the same code, so results must agree to
+rounding and statuses exactly.  collision_solve allocates nothing and does not
+synchronise in the fused mode, so it can be captured in a CUDA graph and
+replayed on new inputs written into the captured buffers.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2601_00976_gb300 import nmc, synthetic
+from gpu_helpers import make_case, to_device, wnorm_errors
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(ctx, p, t):
+    out = ctx.collision_solve(p, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("precision", [nmc.FP64, nmc.MIXED])
+def test_autotune_picks_a_variant_and_keeps_results(precision):
+    edges, g, tables, inp = make_case(16, 1.875, 2, 4, "core_tail", 2048, seed=41)
+    ctx = nmc.Context(edges, 2, 4, tables)
+    t = to_device(inp)
+    tol = 1e-10 if precision == nmc.FP64 else 1e-9
+    p = nmc.default_params(precision=precision, tol_inner=tol, tol_outer=tol)
+    before = _solve(ctx, p, t)
+    minb, pct, ms = ctx.autotune(p, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+    assert minb in (3, 4, 5, 6) and pct in (50, 100) and ms > 0
+    after = _solve(ctx, p, t)
+    assert np.array_equal(before["status"], after["status"])
+    assert np.max(np.abs(before["n_inner"] - after["n_inner"])) <= 2
+    eD, _ = wnorm_errors(after["J"], after["H"], before["J"], before["H"], g.W2)
+    assert eD.max() <= 10 * tol
+    ctx.close()
+
+
+def test_collision_solve_replays_from_a_cuda_graph():
+    N = 1024
+    edges, g, tables, inp = make_case(16, 1.875, 2, 4, "profile", N, seed=42)
+    ctx = nmc.Context(edges, 2, 4, tables)
+    p = nmc.default_params()
+    static = to_device(inp)
+    out = ctx.collision_solve(p, static["rho"], static["T"], static["Ye"], static["D"], static["I"], static["dt"],
+                              static["scale"])
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            ctx.collision_solve(p, static["rho"], static["T"], static["Ye"], static["D"], static["I"], static["dt"],
+                                static["scale"], out=out)
+    torch.cuda.synchronize()
+    for seed in (43, 44, 45):
+        new = synthetic.make_inputs("profile", N, g.eps, 4, seed=seed)
+        for k, v in new.items():
+            static[k].copy_(torch.tensor(v, dtype=torch.float64))
+        graph.replay()
+        torch.cuda.synchronize()
+        ref = _solve(ctx, p, to_device(new))
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        for k in ref:
+            assert np.array_equal(got[k], ref[k]), k
+    ctx.close()
