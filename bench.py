@@ -11,7 +11,12 @@ Inputs (J, H of 268 MB) are larger than L2, so every step reads them from HBM.
 
 The same line carries an "adjoint" object: collision_adjoint (gradients of
 every output with respect to the inputs and the opacity scale factors, FP64)
-over 2^18 nodes of the same profile and grid, timed the same way.
+over 2^18 nodes of the same profile and grid, timed the same way; and a
+"batching" object: the uneven core/tail mix (half rho > 1e13, half rho < 1e10,
+dt log-uniform 1e-7..1e-5 s), FP64, solved by the persistent fused kernel
+(autotuned once, replayed from a CUDA graph) and by plain per-iteration
+launches (NMC_MODE_PLAIN) on the same inputs; 2^17 nodes by default,
+--batching-nodes 4194304 for the full 2^22-node configuration.
 
 Prints one JSON line.  --impl reference times the CPU oracle (the plain FP64
 restatement of the algorithm) on a bounded sample of the same workload.
@@ -44,6 +49,7 @@ TRAFFIC_PER_NODE = {"fused_kernel<double>": 527294720 / 65536, "fused_kernel<flo
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64: 152 SMs x 4 flop/clk x 2.07 GHz (recipe unit count and clock)
 CPU_SAMPLE = 48           # oracle sample (nodes) for the CPU baseline
 ADJ_NODES = 1 << 18
+BATCH_NODES = 1 << 17
 ADJ_WORKLOAD = ("gradient of the FP64 solve (collapse profile, 2^18 nodes, 4 species, Grid C 16x2 energies, "
                 "all processes, forward tol 1e-10) w.r.t. J, H, Ye, T and the 4 opacity scales, "
                 "cotangents on J, H, Ye, eps, T")
@@ -57,6 +63,8 @@ def _args():
     ap.add_argument("--impl", default="nmc", choices=["nmc", "reference"])
     ap.add_argument("--nodes", type=int, default=N_NODES)
     ap.add_argument("--adjoint-nodes", type=int, default=ADJ_NODES, help="0 skips the adjoint measurement")
+    ap.add_argument("--batching-nodes", type=int, default=BATCH_NODES,
+                    help="nodes of the persistent-vs-plain comparison (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="path reported as the headline value (both are timed)")
@@ -255,6 +263,58 @@ def time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream):
                          "algorithmic_flops_per_launch": fl, "kernel_ms": kern_ms}}
 
 
+def time_batching(args, ctx, eps, dev, rank, barrier, allmax, stream):
+    """Persistent fused kernel (autotuned, CUDA-graph replay) vs plain per-iteration launches, FP64."""
+    import torch
+    from paper_2601_00976_gb300 import nmc, synthetic
+    n = args.batching_nodes
+    inp = synthetic.make_inputs("core_tail", n, eps, NS, seed=2000 + rank)
+    t = {k: torch.tensor(v, device=dev) for k, v in inp.items()}
+    p = nmc.default_params(tol_inner=TOL, tol_outer=TOL, m_inner=MEM, m_outer=MEM)
+    minb, pct, _ = ctx.autotune(p, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+    out = ctx.collision_solve(p, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+    barrier()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            ctx.collision_solve(p, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"], out=out)
+    barrier()
+    pp = nmc.default_params(tol_inner=TOL, tol_outer=TOL, m_inner=MEM, m_outer=MEM, mode=nmc.MODE_PLAIN)
+    outp = ctx.collision_solve(pp, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+    res = {}
+    for name, step in (("persistent", lambda: graph.replay()),
+                       ("plain", lambda: ctx.collision_solve(pp, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"],
+                                                             t["scale"], out=outp))):
+        for _ in range(args.warmup):
+            step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+        res[name] = allmax(e0.elapsed_time(e1)) / args.steps
+    ni = out["n_inner"].cpu().numpy()
+    # the two modes run the same algorithm; the tuned variant's rounding can differ, so they agree to tol
+    same_status = float((out["status"] == outp["status"]).float().mean().item())
+    w2 = torch.tensor(ctx.w2, device=dev)
+    refn = torch.sqrt(torch.sum(w2 * out["J"] ** 2, dim=-1))
+    dmax = float(torch.max(torch.sqrt(torch.sum(w2 * (out["J"] - outp["J"]) ** 2, dim=-1)) / refn).item())
+    return {"metric": "converged collision solves/s (nodes*steps/s)", "unit": "solves/s", "dtype": "f64",
+            "config": {"workload": f"core/tail mix, {n} nodes (half rho > 1e13, half rho < 1e10), dt log-uniform "
+                                   "1e-7..1e-5 s, 4 species, Grid C 16x2, all processes, tol 1e-10, Anderson depth 3",
+                       "nodes_per_gpu": n, "inner_iters_min": int(ni.min()), "inner_iters_max": int(ni.max()),
+                       "inner_iters_mean": float(ni.mean()), "tuned_variant": {"blocks_per_sm": minb, "grid_pct": pct},
+                       "status_agreement_persistent_plain": same_status,
+                       "max_rel_J_difference_persistent_plain": dmax},
+            "persistent_graph": {"value": n / (res["persistent"] * 1e-3), "ms_per_step": res["persistent"]},
+            "plain_per_iteration": {"value": n / (res["plain"] * 1e-3), "ms_per_step": res["plain"]},
+            "speedup_persistent_vs_plain": res["plain"] / res["persistent"]}
+
+
 def run_nmc(args):
     import torch
     from paper_2601_00976_gb300 import nmc, flops
@@ -271,6 +331,11 @@ def run_nmc(args):
     p64 = nmc.default_params(tol_inner=TOL, tol_outer=TOL, m_inner=MEM, m_outer=MEM)
     pmx = nmc.default_params(tol_inner=MIXED_TOL[0], tol_outer=MIXED_TOL[1], m_inner=MEM, m_outer=MEM,
                              precision=nmc.MIXED)
+    # the autotuner picks the fused kernel's variant for each precision on this batch (untimed)
+    tuned = {}
+    for name, prm in (("fp64", p64), ("mixed", pmx)):
+        minb, pct, _ = ctx.autotune(prm, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+        tuned[name] = {"blocks_per_sm": minb, "grid_pct": pct}
     o64 = ctx.collision_solve(p64, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
     omx = ctx.collision_solve(pmx, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
 
@@ -338,6 +403,7 @@ def run_nmc(args):
     e2e_s = allmax((time.perf_counter() - t0) / e2e_steps)
 
     adj = time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.adjoint_nodes > 0 else None
+    bat = time_batching(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.batching_nodes > 0 else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -371,6 +437,7 @@ def run_nmc(args):
                        "mixed_max_rel_error_vs_fp64": err,
                        "mean_inner_iters": float(head["n_in"].mean()), "mean_outer_iters": float(head["n_out"].mean()),
                        "max_inner_iters": int(head["n_in"].max()), "nodes_flagged": head["flagged"],
+                       "tuned_variants": tuned,
                        "converged_fraction": head["converged"] / (ws * args.nodes)},
             "roofline": roofmx if headline_mixed else roof64,
             "roofline_fp64": roof64,
@@ -382,6 +449,8 @@ def run_nmc(args):
         }
         if adj is not None:
             line["adjoint"] = adj
+        if bat is not None:
+            line["batching"] = bat
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -114,6 +114,38 @@ __device__ inline void anderson_solve(const double (&G)[MAXM][MAXM], int m, doub
     alpha[L] = 1.0;
     if (m <= 1) return;
     const int n = m - 1;
+    if (n <= 2) {
+        // the same eliminated normal equations and pivot tests in registers (depth <= 3)
+        const int g0 = base, g1 = base + 1;
+        const double a00 = G[g0][g0] - 2.0 * G[g0][L] + G[L][L], r0 = G[L][L] - G[g0][L];
+        if (n == 1) {
+            if (!(fabs(a00) > 1e-14 * fabs(a00)) || !isfinite(a00)) return;
+            const double gam = r0 / a00;
+            if (!isfinite(gam)) return;
+            alpha[g0] = gam;
+            alpha[L] = 1.0 - gam;
+            return;
+        }
+        const double a01 = G[g0][g1] - G[g0][L] - G[g1][L] + G[L][L];
+        const double a11 = G[g1][g1] - 2.0 * G[g1][L] + G[L][L], r1 = G[L][L] - G[g1][L];
+        const double dmax = fmax(fabs(a00), fabs(a11));
+        if (!(dmax > 0.0) || !isfinite(dmax)) return;
+        // column 0 with partial pivoting (the system is symmetric: a10 = a01)
+        double p0 = a00, p1 = a01, pr = r0, q0 = a01, q1 = a11, qr = r1;
+        if (fabs(a01) > fabs(a00)) { p0 = a01; p1 = a11; pr = r1; q0 = a00; q1 = a01; qr = r0; }
+        if (!(fabs(p0) > 1e-14 * dmax)) return;
+        const double f = q0 / p0;
+        const double s11 = q1 - f * p1, sr = qr - f * pr;
+        if (!(fabs(s11) > 1e-14 * dmax)) return;
+        const double gam1 = sr / s11;
+        const double gam0 = (pr - p1 * gam1) / p0;
+        const double sum = gam0 + gam1;
+        if (!isfinite(sum)) return;
+        alpha[g0] = gam0;
+        alpha[g1] = gam1;
+        alpha[L] = 1.0 - sum;
+        return;
+    }
     double A[MAXM][MAXM + 1];
     double dmax = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -196,12 +228,13 @@ struct OpacBufs {
 //    q >= q' and completed by detailed balance, K_Out[q'][q] = a_q / a_q'
 //    K_Out[q][q'] for q' < q (Eqs. inOutInvarianceNES, detailedBalanceNES),
 //    and the pair kernel K_Ann of each particle/antiparticle pair.
-// Thread 0 ORs NMC_TABLE_CLAMP into *status when a lookup leaves a table.
+// Thread `lead` does the scalar part and ORs NMC_TABLE_CLAMP into *status when a
+// lookup leaves a table.
 // Ends with the block synchronised.
 template <typename R>
 __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const nmc_params& P, double rho,
                                   double T, double Ye, double dtau, const double* sc, const OpacBufs<R>& b,
-                                  OpacState* os, int* status, R& chiab, R& sig, R& deq, R& deqc) {
+                                  OpacState* os, int* status, R& chiab, R& sig, R& deq, R& deqc, int lead = 0) {
     constexpr bool kMixed = sizeof(R) == 4;
     const int NS = g.ns, NE = g.ne, NEP = g.nep, LD = g.ld;
     const int tid = threadIdx.x;
@@ -212,7 +245,7 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
     const bool pair_on = (P.proc_mask & NMC_PROC_PAIR) != 0;
     R* fq = b.phi;
 
-    if (tid == 0) {
+    if (tid == lead) {
         double mu_e, mnu;
         if (kMixed) {
             // FP32 root of the electron cubic, then one FP64 Newton step on it (the error

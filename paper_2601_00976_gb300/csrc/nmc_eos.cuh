@@ -41,37 +41,42 @@ __device__ __forceinline__ void eos_eps(double rho, double T, double Ye, double*
     *deps = (due + 1.5 * nb + 4.0 * pi2 / 15.0 * T2 * T / hc3) * f;
 }
 
-// T with eps(rho, T, Ye) = eps_t: safeguarded Newton in T, bracketed by
-// [kTMin, kTMax].  *ok = false (and T clamped) when eps_t is outside the range.
+// T with eps(rho, T, Ye) = eps_t: safeguarded Newton in T within [kTMin, kTMax].
+// The bracket starts as the whole range without evaluating its ends (a warm
+// start from the previous T needs ~3 evaluations); every evaluation narrows it,
+// and a Newton step that leaves it is replaced by a geometric bisection.
+// eps is strictly increasing in T, so an eps_t outside [eps(kTMin), eps(kTMax)]
+// drives the iterate to a range end: *ok = false and T clamped there.
 __device__ inline double eos_temperature(double rho, double eps_t, double Ye, double T0, bool* ok) {
     *ok = true;
     if (!(Ye > 0.0 && Ye < 1.0) || !isfinite(eps_t)) {
         *ok = false;
         return isfinite(T0) ? T0 : 1.0;
     }
-    double lo = kTMin, hi = kTMax, e, de;
-    eos_eps(rho, lo, Ye, &e, &de);
-    if (eps_t <= e) { *ok = false; return lo; }
-    eos_eps(rho, hi, Ye, &e, &de);
-    if (eps_t >= e) { *ok = false; return hi; }
+    double lo = kTMin, hi = kTMax, e, de, f = 0.0;
     double T = (T0 > lo && T0 < hi) ? T0 : sqrt(lo * hi);
-    for (int it = 0; it < 200; ++it) {
+    for (int it = 0; it < 300; ++it) {
         eos_eps(rho, T, Ye, &e, &de);
-        const double f = e - eps_t;
+        f = e - eps_t;
         if (f > 0.0) hi = T; else lo = T;
         if (f == 0.0) break;
         double Tn = T - f / de;
-        if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+        if (!(Tn > lo && Tn < hi)) Tn = hi > 2.0 * lo ? sqrt(lo * hi) : 0.5 * (lo + hi);
         const double d = fabs(Tn - T);
         T = Tn;
         if (d <= 2e-16 * T || hi - lo <= 4e-16 * hi) break;
     }
+    if (f > 0.0 && T <= kTMin * (1.0 + 1e-12)) {   // eps_t below eps(kTMin)
+        eos_eps(rho, kTMin, Ye, &e, &de);
+        if (eps_t <= e) { *ok = false; return kTMin; }
+    }
+    if (f < 0.0 && T >= kTMax * (1.0 - 1e-12)) {   // eps_t above eps(kTMax)
+        eos_eps(rho, kTMax, Ye, &e, &de);
+        if (eps_t >= e) { *ok = false; return kTMax; }
+    }
     return T;
 }
 
-// d eps / d Ye at fixed rho, T (erg/g): only the electrons depend on Ye, with
-// d n_e / d Ye = rho / m_B and, at fixed T,
-// d u_e / d n_e = (du_e/dmu) / (dn_e/dmu) = 3 mu (mu^2 + pi^2 T^2) / (3 mu^2 + pi^2 T^2).
 __device__ __forceinline__ double eos_deps_dye(double rho, double T, double Ye) {
     const double pi2 = kPi * kPi;
     const double mu = eos_mu_e(rho, T, Ye);

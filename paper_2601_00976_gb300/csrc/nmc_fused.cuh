@@ -136,6 +136,11 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         __syncthreads();
         const long long n = nd->node;
         if (n >= a.n) break;
+        // The node's scalar work (EoS, least squares, matter update) runs in lane 0 of one
+        // warp.  A warp's FP64 instruction holds its SMSP's FP64 pipe ~64 cycles however
+        // few lanes are active, and warp w of every resident block sits on the same SMSP,
+        // so the lead warp rotates with the node to spread that work over the SMSPs.
+        const int lead = (int)(n % (long long)(blockDim.x >> 5)) << 5;
 
         // ---------------- node set-up ----------------
         double Dsd = 0.0, Isd[3] = {0.0, 0.0, 0.0};
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
             Isd[1] = a.H[o * 3 + 1];
             Isd[2] = a.H[o * 3 + 2];
         }
-        if (tid == 0) {
+        if (tid == lead) {
             const double rho = a.rho[n], T = a.T[n], Ye = a.Ye[n], dt = a.dt[n];
             nd->rho = rho;
             nd->T = T;
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                 a.J_out[o] = Dsd;
                 for (int j = 0; j < 3; ++j) a.H_out[o * 3 + j] = Isd[j];
             }
-            if (tid == 0) {
+            if (tid == lead) {
                 a.Ye_out[n] = a.Ye[n];
                 a.eps_out[n] = nd->ystar[0];
                 a.T_out[n] = a.T[n];
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         {   // E_nu*, N_nu* in FP64 (Eqs. eulerianEnergyLG, eulerianNumberLG at v = 0)
             double v[2] = {W3q * Dsd, gs * W2q * Dsd};
             block_sum<2, double>(v, red, nd->blk_out);
-            if (tid == 0) { nd->EN_star[0] = nd->blk_out[0]; nd->EN_star[1] = nd->blk_out[1]; }
+            if (tid == lead) { nd->EN_star[0] = nd->blk_out[0]; nd->EN_star[1] = nd->blk_out[1]; }
         }
         const R Ds = (R)Dsd;
         const R Is[3] = {(R)Isd[0], (R)Isd[1], (R)Isd[2]};
@@ -199,13 +204,13 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         for (int k = 1;; ++k) {
             // ================= ComputeOpacities(y^[k]) =================
             compute_opacities<R>(g, a.tb, P, nd->rho, nd->T, nd->y[1], nd->dtau, nd->sc, ob, &nd->op,
-                                 &nd->status, chiab, sig, deq, deqc);
+                                 &nd->status, chiab, sig, deq, deqc, lead);
             // reference norm ||D^[k,1]||_W per species (Algorithm 2 input)
             {
                 R v[1] = {Wt * M[0] * M[0]};
                 R* out = reinterpret_cast<R*>(nd->sp_out);
                 species_sum<1, R>(v, red, out, NEP, NS);
-                if (tid == 0) {
+                if (tid == lead) {
                     const double fl = P.norm_floor * sqrt(g.sum_wt);
                     for (int sp = 0; sp < NS; ++sp) nd->dnorm[sp] = fmax((double)r_sqrt(out[sp]), fl);
                 }
@@ -334,7 +339,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         v[j] = F[0] * Fh[j][0] + F[1] * Fh[j][1] + F[2] * Fh[j][2] + F[3] * Fh[j][3];
                     R* out = reinterpret_cast<R*>(nd->blk_out);
                     block_sum<MAXM, R>(v, red, out);
-                    if (tid == 0) {
+                    if (tid == lead) {
                         for (int i = 0; i < MAXM - 1; ++i)
                             for (int j = 0; j < MAXM - 1; ++j) nd->G[i][j] = nd->G[i + 1][j + 1];
                         for (int j = 0; j < MAXM; ++j) {
@@ -377,7 +382,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         nd->bad = 1;
                     R* out = reinterpret_cast<R*>(nd->sp_out);
                     species_sum<4, R>(v, red, out, NEP, NS);
-                    if (tid == 0) {
+                    if (tid == lead) {
                         int conv = 1;
                         // mixed precision: D is an FP64 iterate and is held to tol_inner; the first
                         // moments are FP32 values, checked against FP32 resolution at the finest
@@ -407,7 +412,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                 const double Dcur = kMixed ? Dd : (double)M[0];
                 double v[2] = {W3q * Dcur, gs * W2q * Dcur};
                 block_sum<2, double>(v, red, nd->blk_out);
-                if (tid == 0) {
+                if (tid == lead) {
                     const double rho = nd->rho;
                     const double qv0 = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * kMeVErg / rho;
                     const double qv1 = nd->ystar[1] - kMB * (nd->blk_out[1] - nd->EN_star[1]) / rho;
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                 if (nd->conv_out) outer_exit = 1;
             }
             if (outer_exit) {
-                if (tid == 0) nd->n_outer = k;
+                if (tid == lead) nd->n_outer = k;
                 break;
             }
         }
@@ -459,12 +464,12 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
             const double Dcur = kMixed ? Dd : (double)M[0];
             double v[2] = {W3q * Dcur, gs * W2q * Dcur};
             block_sum<2, double>(v, red, nd->blk_out);
-            if (tid == 0) {
+            if (tid == lead) {
                 nd->qv[0] = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * kMeVErg / nd->rho;
                 nd->qv[1] = nd->ystar[1] - kMB * (nd->blk_out[1] - nd->EN_star[1]) / nd->rho;
             }
         }
-        if (tid == 0) {
+        if (tid == lead) {
             const double rho = nd->rho;
             double yo0, yo1, To;
             if (P.frozen_matter) {
