@@ -130,15 +130,18 @@ __device__ inline void anderson_solve(const double (&G)[MAXM][MAXM], int m, doub
         const double a11 = G[g1][g1] - 2.0 * G[g1][L] + G[L][L], r1 = G[L][L] - G[g1][L];
         const double dmax = fmax(fabs(a00), fabs(a11));
         if (!(dmax > 0.0) || !isfinite(dmax)) return;
-        // column 0 with partial pivoting (the system is symmetric: a10 = a01)
+        // Column 0 with partial pivoting (the system is symmetric: a10 = a01); the pivot tests of
+        // the elimination, |p0| and |s11| = |det / p0| against 1e-14 dmax, need no division, and
+        // Cramer's rule then needs one: a single-lane FP64 division is a long chain of FP64-pipe
+        // instructions on the solve's critical path.
         double p0 = a00, p1 = a01, pr = r0, q0 = a01, q1 = a11, qr = r1;
         if (fabs(a01) > fabs(a00)) { p0 = a01; p1 = a11; pr = r1; q0 = a00; q1 = a01; qr = r0; }
         if (!(fabs(p0) > 1e-14 * dmax)) return;
-        const double f = q0 / p0;
-        const double s11 = q1 - f * p1, sr = qr - f * pr;
-        if (!(fabs(s11) > 1e-14 * dmax)) return;
-        const double gam1 = sr / s11;
-        const double gam0 = (pr - p1 * gam1) / p0;
+        const double det = p0 * q1 - q0 * p1;
+        if (!(fabs(det) > 1e-14 * dmax * fabs(p0))) return;
+        const double rdet = 1.0 / det;
+        const double gam1 = (p0 * qr - q0 * pr) * rdet;
+        const double gam0 = (pr * q1 - p1 * qr) * rdet;
         const double sum = gam0 + gam1;
         if (!isfinite(sum)) return;
         alpha[g0] = gam0;
