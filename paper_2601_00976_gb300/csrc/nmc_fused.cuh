@@ -116,11 +116,12 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
     const double W3q = act ? g.w3[q] : 0.0;
     const R Wt = act ? (kMixed ? (R)g.wt_f[q] : (R)g.wt[q]) : (R)0;
 
-    // Mixed precision keeps the number moment D and its map values in FP64
-    // (QhD): near a fixed point where 1 + dtau chi ~ 1e4, FP32 increments of D
-    // fall below one ulp long before the equation residual is small.
+    // Mixed precision keeps the number moment D in FP64 (near a fixed point where
+    // 1 + dtau chi ~ 1e4, FP32 increments of D fall below one ulp long before the
+    // equation residual is small) and its Anderson history Qh[.][0] as FP32
+    // offsets Q_j - D from the current iterate, which are small near convergence:
+    // the mixing then costs one FP64 add instead of FP64 arithmetic on the window.
     R Fh[MAXM][4], Qh[MAXM][4];
-    double QhD[kMixed ? MAXM : 1];
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
 #pragma unroll
@@ -128,8 +129,6 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) Qh[j][c] = 0;
     }
-#pragma unroll
-    for (int j = 0; j < (kMixed ? MAXM : 1); ++j) QhD[j] = 0.0;
 
     for (;;) {
         if (tid == 0) nd->node = atomicAdd(a.queue, 1);
@@ -198,6 +197,8 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         const R Is[3] = {(R)Isd[0], (R)Isd[1], (R)Isd[2]};
         R M[4] = {Ds, Is[0], Is[1], Is[2]};
         double Dd = Dsd;   // FP64 number moment (mixed precision); M[0] is its FP32 shadow
+        // mixed: per outer iteration, numerator W~ (D* - D) + W~ dtau chi_EmAb (D^Eq - D) = A0 - c12 D
+        double A0 = 0.0, c12 = 0.0, deq_d = 0.0;
         R chiab = 0, sig = 0, deq = 0, deqc = 0;
         int outer_exit = 0;
 
@@ -205,6 +206,12 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
             // ================= ComputeOpacities(y^[k]) =================
             compute_opacities<R>(g, a.tb, P, nd->rho, nd->T, nd->y[1], nd->dtau, nd->sc, ob, &nd->op,
                                  &nd->status, chiab, sig, deq, deqc, lead);
+            if constexpr (kMixed) {
+                deq_d = (double)deq;
+                const double c1 = (double)Wt, c2 = c1 * (double)chiab;
+                A0 = c1 * Dsd + c2 * deq_d;
+                c12 = c1 + c2;
+            }
             // reference norm ||D^[k,1]||_W per species (Algorithm 2 input)
             {
                 R v[1] = {Wt * M[0] * M[0]};
@@ -224,11 +231,10 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                     vWD[sq] = Wt * M[0];
                     vW1D[sq] = Wt * hole;
                     vAW1D[sq] = vA[sq] * Wt * hole;
-                    if constexpr (kMixed) vWdev[sq] = (R)(Dd - (double)deq) * (Wt / deqc);
+                    if constexpr (kMixed) vWdev[sq] = (R)(Dd - deq_d) * (Wt / deqc);
                 }
                 __syncthreads();
                 R F[4] = {0, 0, 0, 0}, Qv[4] = {0, 0, 0, 0};
-                double QD = 0.0;   // mixed: Q_D in FP64
                 R dlt = 0;         // mixed: Q_D - D, formed without cancellation
                 if (act) {
                     R nin = 0, nout = 0, pro = 0, an = 0;
@@ -301,13 +307,12 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         // with the net collision term W~ dtau C = W~ dtau chi_EmAb (D^Eq - D) + net NES
                         // + net pair exchanges.  The numerator, whose zero is the fixed point, is
                         // summed in FP64 around the FP64 D; the denominator only scales the step, so
-                        // FP32 rounding in chi does not move the fixed point.
-                        const double numW = (double)Wt * ((Dsd - Dd) + (double)chiab * ((double)deq - Dd)) +
-                                            ((double)cn + (double)cp);
+                        // FP32 rounding in chi does not move the fixed point.  The history holds
+                        // Q_D - D (the offset of the map value from the current iterate).
+                        const double numW = fma(-c12, Dd, A0) + (double)(cn + cp);
                         const R inv = (R)1 / ((R)1 + chi);
                         dlt = (R)numW * (inv / Wt);
-                        QD = Dd + (double)dlt;
-                        Qv[0] = (R)QD;
+                        Qv[0] = dlt;
                     } else {
                         Qv[0] = (Ds + eta) / ((R)1 + chi);          // Eq. implicitMomentsNodal, v = 0
                     }
@@ -326,11 +331,6 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) { Fh[MAXM - 1][c] = F[c]; Qh[MAXM - 1][c] = Qv[c]; }
-                if constexpr (kMixed) {
-#pragma unroll
-                    for (int j = 0; j < MAXM - 1; ++j) QhD[j] = QhD[j + 1];
-                    QhD[MAXM - 1] = QD;
-                }
                 const int m = ell < P.m_inner ? ell : P.m_inner;
                 {   // new row of the Gram matrix; least squares in FP64 (thread 0)
                     R v[MAXM];
@@ -362,23 +362,25 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                     Mn[c] = act ? acc : (R)0;
                 }
                 double Ddn = Dd;
+                R sD = 0;   // mixed: D^new - D
                 if constexpr (kMixed) {
-                    // D in FP64 and in difference form, Q_L + sum_j alpha_j (Q_j - Q_L): the
-                    // rounding of alpha then scales only the small differences of the window
-                    double accd = QhD[MAXM - 1];
+                    // in difference form, o_L + sum_j alpha_j (o_j - o_L) with o = Q - D: the
+                    // rounding of alpha scales only the small differences of the window
+                    R acc = Qh[MAXM - 1][0];
 #pragma unroll
                     for (int j = 0; j < MAXM - 1; ++j)
-                        if (j >= MAXM - m) accd = fma(nd->alpha[j], QhD[j] - QhD[MAXM - 1], accd);
-                    Ddn = act ? accd : 0.0;
+                        if (j >= MAXM - m) acc = r_fma((R)nd->alpha_f[j], Qh[j][0] - Qh[MAXM - 1][0], acc);
+                    sD = act ? acc : (R)0;
+                    Ddn = Dd + (double)sD;
                     Mn[0] = (R)Ddn;
                 }
                 {   // Algorithm 2: per species, W-weighted squares of the change per moment
                     R v[4];
 #pragma unroll
                     for (int c = 0; c < 4; ++c) { const R d = Mn[c] - M[c]; v[c] = Wt * d * d; }
-                    if constexpr (kMixed) { const R d = (R)(Ddn - Dd); v[0] = Wt * d * d; }
+                    if constexpr (kMixed) v[0] = Wt * sD * sD;
                     if (act && !(isfinite(Mn[0]) && isfinite(Mn[1]) && isfinite(Mn[2]) && isfinite(Mn[3]) &&
-                                 isfinite(Ddn)))
+                                 isfinite(sD)))
                         nd->bad = 1;
                     R* out = reinterpret_cast<R*>(nd->sp_out);
                     species_sum<4, R>(v, red, out, NEP, NS);
@@ -403,6 +405,10 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) M[c] = Mn[c];
                 Dd = Ddn;
+                if constexpr (kMixed) {   // offsets now relative to the new iterate
+#pragma unroll
+                    for (int j = 0; j < MAXM; ++j) Qh[j][0] -= sD;
+                }
                 if (nd->conv_in) break;
             }
             // an inner loop stopped at its cap (or a non-finite moment) ends the node
