@@ -389,23 +389,28 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         const long long mat = (long long)NE * NE;
         const long long sE = mat, sT = (long long)tb.eta.n * mat;
         const double unit = kMixed ? dtau : dtau * kCW;   // FP32 tables carry 4 pi/(hc)^3
-        if (nes_on && act) {
+        if (nes_on && s < NS) {
             const R c = (R)(unit * sc[2]);
             const long long off = (((long long)s * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
             R* P0 = b.phi + s * NE * LD;
-            for (int r = 0; r < NE; ++r) {   // lower triangle incl. diagonal; row r read coalesced
-                if (q <= r) {
-                    const long long o = off + (long long)r * NE + q;
-                    R v;
-                    if (kMixed) {
-                        const float* t = tb.nes_f;
-                        v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
-                    } else {
-                        const double* t = tb.nes;
-                        v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
-                    }
-                    P0[r * LD + q] = c * v;
+            // lower triangle incl. diagonal, entries enumerated row by row so that every lane of the
+            // species group has one (a row loop with q <= r leaves half the lanes idle)
+            const int ntri = NE * (NE + 1) / 2;
+            for (int idx = q; idx < ntri; idx += NEP) {
+                int r = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+                while (r * (r + 1) / 2 > idx) --r;
+                while ((r + 1) * (r + 2) / 2 <= idx) ++r;
+                const int cc = idx - r * (r + 1) / 2;
+                const long long o = off + (long long)r * NE + cc;
+                R v;
+                if (kMixed) {
+                    const float* t = tb.nes_f;
+                    v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
+                } else {
+                    const double* t = tb.nes;
+                    v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
                 }
+                P0[r * LD + cc] = c * v;
             }
         }
         if (pair_on && s < NS) {
@@ -428,10 +433,18 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
             }
         }
         __syncthreads();
-        if (nes_on && act) {   // up-scattering by detailed balance: K[r][q] = a_q / a_r K[q][r], r < q
+        if (nes_on && s < NS) {   // up-scattering by detailed balance: K[r][c] = a_c / a_r K[c][r], r < c
             R* P0 = b.phi + s * NE * LD;
-            const R aq = b.vA[sq];
-            for (int r = 0; r < q; ++r) P0[r * LD + q] = aq * b.vAi[s * NEP + r] * P0[q * LD + r];
+            const R* va = b.vA + s * NEP;
+            const R* vai = b.vAi + s * NEP;
+            const int nup = NE * (NE - 1) / 2;   // strictly upper entries, column by column
+            for (int idx = q; idx < nup; idx += NEP) {
+                int cc = (int)((sqrtf(8.0f * idx + 1.0f) + 1.0f) * 0.5f);
+                while (cc * (cc - 1) / 2 > idx) --cc;
+                while ((cc + 1) * cc / 2 <= idx) ++cc;
+                const int r = idx - cc * (cc - 1) / 2;
+                P0[r * LD + cc] = va[cc] * vai[r] * P0[cc * LD + r];
+            }
         }
     }
     __syncthreads();

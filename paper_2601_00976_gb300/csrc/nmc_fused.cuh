@@ -313,10 +313,16 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         const R inv = (R)1 / ((R)1 + chi);
                         dlt = (R)numW * (inv / Wt);
                         Qv[0] = dlt;
-                    } else {
-                        Qv[0] = (Ds + eta) / ((R)1 + chi);          // Eq. implicitMomentsNodal, v = 0
                     }
-                    const R fI = (R)1 / ((R)1 + kap);
+                    R fI;
+                    if constexpr (kMixed) {
+                        fI = (R)1 / ((R)1 + kap);
+                    } else {
+                        // Eq. implicitMomentsNodal at v = 0, both quotients from one FP64 division
+                        const R d1 = (R)1 + chi, d2 = (R)1 + kap, rr = (R)1 / (d1 * d2);
+                        Qv[0] = (Ds + eta) * d2 * rr;
+                        fI = d1 * rr;
+                    }
                     Qv[1] = Is[0] * fI;
                     Qv[2] = Is[1] * fI;
                     Qv[3] = Is[2] * fI;

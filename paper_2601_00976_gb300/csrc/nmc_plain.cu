@@ -285,8 +285,10 @@ __global__ void __launch_bounds__(512) plain_inner_kernel(const SolveArgs a, Pla
             const double eta = chiab * deq + nin + pro;
             const double chi = chiab + nin + nout + pro + an;
             const double kap = chi + sig;
-            Qv[0] = (Ds + eta) / (1.0 + chi);          // Eq. implicitMomentsNodal, v = 0
-            const double fI = 1.0 / (1.0 + kap);
+            // Eq. implicitMomentsNodal at v = 0, both quotients from one division (as the fused kernel)
+            const double d1 = 1.0 + chi, d2 = 1.0 + kap, rr = 1.0 / (d1 * d2);
+            Qv[0] = (Ds + eta) * d2 * rr;
+            const double fI = d1 * rr;
             for (int c = 0; c < 3; ++c) Qv[1 + c] = Is[c] * fI;
             for (int c = 0; c < 4; ++c) F[c] = Qv[c] - M[c];
         }
