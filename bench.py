@@ -44,8 +44,8 @@ WORKLOAD = ("collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, EmAb
             "FP64, Anderson depth 3, tol 1e-10")
 # DRAM bytes (read + write) per node of one launch, from ncu captures of the 2^16-node profile
 # (dram__bytes_read.sum + dram__bytes_write.sum); traffic grows with the node count
-TRAFFIC_PER_NODE = {"fused_kernel<double>": 527294720 / 65536, "fused_kernel<float>": 512146944 / 65536,
-                    "adjoint_kernel": 875269376 / 65536}
+TRAFFIC_PER_NODE = {"fused_kernel<double>": 539470848 / 65536, "fused_kernel<float>": 598283776 / 65536,
+                    "adjoint_kernel": 873628672 / 65536}
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64: 152 SMs x 4 flop/clk x 2.07 GHz (recipe unit count and clock)
 CPU_SAMPLE = 48           # oracle sample (nodes) for the CPU baseline
 ADJ_NODES = 1 << 18
