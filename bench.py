@@ -143,10 +143,8 @@ class ClockSampler:
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2601_00976_gb300.dist import world
+    return world()
 
 
 def run_reference(args):
@@ -224,7 +222,9 @@ def time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream):
     import torch
     from paper_2601_00976_gb300 import nmc, synthetic, flops
     n = args.adjoint_nodes
-    inp = synthetic.make_inputs("profile", n, eps, NS, seed=1000 + rank)
+    from paper_2601_00976_gb300.dist import workload_seed, weak_scaling_value
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    inp = synthetic.make_inputs("profile", n, eps, NS, seed=workload_seed(rank, 1))
     t = {k: torch.tensor(v, device=dev) for k, v in inp.items()}
     p = nmc.default_params(tol_inner=TOL, tol_outer=TOL, m_inner=MEM, m_outer=MEM)
     fw = ctx.collision_solve(p, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
@@ -253,7 +253,7 @@ def time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream):
     clean = int(torch.count_nonzero((out["status"] & ~nmc.TABLE_CLAMP) == 0).item())
     fl = flops.adjoint_flops(NS, len(eps), N_ELEM, NQ) * n
     ach = fl / (kern_ms * 1e-3) / 1e12
-    return {"metric": "node gradients/s (nodes*steps/s)", "value": n * args.steps / (total_ms * 1e-3),
+    return {"metric": "node gradients/s (nodes*steps/s)", "value": weak_scaling_value(ws * n, args.steps, total_ms),
             "unit": "nodes/s", "ms_per_step": total_ms / args.steps, "dtype": "f64",
             "config": {"workload": ADJ_WORKLOAD, "nodes_per_gpu": n, "clean_fraction": clean / n},
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -268,7 +268,9 @@ def time_batching(args, ctx, eps, dev, rank, barrier, allmax, stream):
     import torch
     from paper_2601_00976_gb300 import nmc, synthetic
     n = args.batching_nodes
-    inp = synthetic.make_inputs("core_tail", n, eps, NS, seed=2000 + rank)
+    from paper_2601_00976_gb300.dist import workload_seed
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    inp = synthetic.make_inputs("core_tail", n, eps, NS, seed=workload_seed(rank, 2))
     t = {k: torch.tensor(v, device=dev) for k, v in inp.items()}
     p = nmc.default_params(tol_inner=TOL, tol_outer=TOL, m_inner=MEM, m_outer=MEM)
     minb, pct, _ = ctx.autotune(p, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
@@ -310,21 +312,21 @@ def time_batching(args, ctx, eps, dev, rank, barrier, allmax, stream):
                        "inner_iters_mean": float(ni.mean()), "tuned_variant": {"blocks_per_sm": minb, "grid_pct": pct},
                        "status_agreement_persistent_plain": same_status,
                        "max_rel_J_difference_persistent_plain": dmax},
-            "persistent_graph": {"value": n / (res["persistent"] * 1e-3), "ms_per_step": res["persistent"]},
-            "plain_per_iteration": {"value": n / (res["plain"] * 1e-3), "ms_per_step": res["plain"]},
+            "persistent_graph": {"value": ws * n / (res["persistent"] * 1e-3), "ms_per_step": res["persistent"]},
+            "plain_per_iteration": {"value": ws * n / (res["plain"] * 1e-3), "ms_per_step": res["plain"]},
             "speedup_persistent_vs_plain": res["plain"] / res["persistent"]}
 
 
 def run_nmc(args):
     import torch
     from paper_2601_00976_gb300 import nmc, flops
+    from paper_2601_00976_gb300.dist import Group, workload_seed, weak_scaling_value
     ws, rank, local = _dist()
     if ws > 1:
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", torch.cuda.current_device())
-    edges, eps, tables, inp = _workload(rank, args.nodes)
+    group = Group(dev)
+    edges, eps, tables, inp = _workload(workload_seed(rank, 0), args.nodes)
     ctx = nmc.Context(edges, NQ, NS, tables)
     t = {k: torch.tensor(v, device=dev) for k, v in inp.items()}
     stream = torch.cuda.current_stream()
@@ -339,25 +341,7 @@ def run_nmc(args):
     o64 = ctx.collision_solve(p64, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
     omx = ctx.collision_solve(pmx, t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
 
-    def barrier():
-        torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    def allmax(x):
-        if ws == 1:
-            return x
-        tt = torch.tensor([x], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        return tt.item()
-
-    def allsum(x):
-        if ws == 1:
-            return x
-        tt = torch.tensor([x], device=dev, dtype=torch.int64)
-        torch.distributed.all_reduce(tt)
-        return int(tt.item())
+    barrier, allmax, allsum = group.barrier, group.allmax, group.allsum
 
     headline_mixed = args.precision == "mixed"
     clk = ClockSampler(dev.index)
@@ -409,8 +393,8 @@ def run_nmc(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(edges, tables, inp)
     if rank == 0:
-        def line_value(r):
-            return r["converged"] * args.steps / (r["total_ms"] * 1e-3)
+        def line_value(r):   # converged nodes of every rank per step, over the slowest rank's time
+            return weak_scaling_value(r["converged"], args.steps, r["total_ms"])
 
         def roof(r, peak, kernel, note):
             ach = r["flops"] / (r["kern_ms"] * 1e-3) / 1e12
@@ -455,8 +439,7 @@ def run_nmc(args):
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     ctx.close()
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    group.close()
 
 
 def main():
