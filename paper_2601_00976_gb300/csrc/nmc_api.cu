@@ -286,6 +286,11 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
     if (rc == NMC_OK) rc = upload(ctx, wt.data(), ne, &g.wt);
     if (rc == NMC_OK) rc = upload_f32(ctx, wt.data(), ne, 1.0, &g.wt_f);
     if (rc == NMC_OK) rc = upload_f32(ctx, pe.data(), pe.size(), 1.0, &g.proj_e_f);
+    if (rc == NMC_OK) {
+        std::vector<double> lo(pe.size());
+        for (size_t i = 0; i < pe.size(); ++i) lo[i] = pe[i] - (double)(float)pe[i];
+        rc = upload_f32(ctx, lo.data(), lo.size(), 1.0, &g.proj_e_fl);
+    }
     if (rc == NMC_OK) rc = upload_f32(ctx, pc.data(), pc.size(), 1.0, &g.proj_c_f);
     if (rc == NMC_OK) rc = upload_f32(ctx, pa.data(), pa.size(), 1.0, &g.proj_a_f);
     if (rc == NMC_OK) rc = upload(ctx, ctx->w2.data(), ne, &g.w2);

@@ -52,6 +52,85 @@ __device__ __forceinline__ void block_sum(T (&v)[K], void* scratch, T* out) {
     __syncthreads();
 }
 
+// ---- double-float: an unevaluated sum h + l of two FP32 words ----
+// Carries about 48 significant bits in FP32 arithmetic (Dekker, Numer. Math. 18,
+// 1971).  two_sum is Knuth's error-free addition (TAOCP vol. 2, 4.2.2): s + e
+// equals a + b exactly for any magnitudes.  The _rn intrinsics keep the
+// compiler from contracting or reassociating the error terms.
+struct F2 {
+    float h, l;
+};
+
+__device__ __forceinline__ F2 f2_from(double x) {
+    F2 r;
+    r.h = (float)x;
+    r.l = (float)(x - (double)r.h);
+    return r;
+}
+
+__device__ __forceinline__ double f2_to(F2 a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ float two_sum(float a, float b, float* e) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    *e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// a + b for a float b, renormalised so that |l| <= ulp(h) / 2
+__device__ __forceinline__ F2 f2_add(F2 a, float b) {
+    float e, e2;
+    const float s = two_sum(a.h, b, &e);
+    F2 r;
+    r.h = two_sum(s, __fadd_rn(e, a.l), &e2);
+    r.l = e2;
+    return r;
+}
+
+// A - c x + t with A, c, x double-float and t a float.  Near a root the terms
+// cancel: A - c x keeps ~2^-48 |A| absolute error (the high product is exact by
+// two-product with an FMA, and A.h - p is exact once they are within a factor
+// of two), and t is added to the high part first, which it cancels.
+__device__ __forceinline__ float f2_residual(F2 A, F2 c, F2 x, float t) {
+    const float p = __fmul_rn(c.h, x.h);
+    float pe = fmaf(c.h, x.h, -p);   // c.h x.h = p + pe exactly
+    pe = fmaf(c.h, x.l, pe);
+    pe = fmaf(c.l, x.h, pe);
+    float e;
+    const float s = two_sum(A.h, -p, &e);
+    return __fadd_rn(__fadd_rn(s, t), __fadd_rn(e, __fsub_rn(A.l, pe)));
+}
+
+// block_sum split at its first barrier: warp w's sums of the K values land in
+// scratch[w * K + k]; after a barrier, sum_partials in any one thread adds the
+// warps' partials in the order block_sum uses.
+template <int K, typename T>
+__device__ __forceinline__ void warp_partials(T (&v)[K], void* scratch) {
+    T* red = static_cast<T*>(scratch);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(kFull, v[k], off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[w * K + k] = v[k];
+    }
+}
+
+template <int K, typename T>
+__device__ __forceinline__ void sum_partials(const void* scratch, T (&out)[K]) {
+    const T* red = static_cast<const T*>(scratch);
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        T s = 0;
+        for (int i = 0; i < nw; ++i) s += red[i * K + k];
+        out[k] = s;
+    }
+}
+
 // Sum K values over each species group (threads s*nep .. s*nep+nep-1);
 // result in out[s*K + k].  nep is a power of two <= 32 or a multiple of 32.
 template <int K, typename T>
@@ -186,6 +265,86 @@ __device__ inline void anderson_solve(const double (&G)[MAXM][MAXM], int m, doub
     alpha[L] = 1.0 - sum;
 }
 
+// Inner Anderson least squares at depth <= 3, run by all 32 lanes of one warp:
+// the steps of anderson_solve's n <= 2 branch (same pivot tests, Cramer's rule)
+// with the independent FP64 products of a step on different lanes, so that a
+// step costs one warp instruction (an FP64 instruction holds its SMSP's FP64
+// pipe ~64 cycles however few lanes are active).  Lane k < 5 passes entry k of
+// (a00, a01, a11, r0, r1), the eliminated normal equations A gamma = r with
+// A_ij = <F_L - F_gi, F_L - F_gj> and r_i = <F_L - F_gi, F_L> over the window
+// g0 < g1 < L of n + 1 = m columns.  Every lane gets the coefficients (c0, c1,
+// cL) of columns g0, g1 (n = 2) and L; a numerically singular system gives the
+// Picard step (0, 0, 1).
+__device__ __forceinline__ void anderson3_warp(double e, int n, double& c0, double& c1, double& cL) {
+    const int lane = threadIdx.x & 31;
+    const double a00 = __shfl_sync(kFull, e, 0), a01 = __shfl_sync(kFull, e, 1);
+    const double a11 = __shfl_sync(kFull, e, 2), r0 = __shfl_sync(kFull, e, 3);
+    const double r1 = __shfl_sync(kFull, e, 4);
+    c0 = 0.0;
+    c1 = 0.0;
+    cL = 1.0;
+    if (n == 1) {
+        if (fabs(a00) > 1e-14 * fabs(a00) && isfinite(a00)) {
+            const double gam = r0 / a00;
+            if (isfinite(gam)) { c0 = gam; cL = 1.0 - gam; }
+        }
+    } else if (n == 2) {
+        const double dmax = fmax(fabs(a00), fabs(a11));
+        if (dmax > 0.0 && isfinite(dmax)) {
+            // column 0 with partial pivoting (A is symmetric: a10 = a01)
+            const bool sw = fabs(a01) > fabs(a00);
+            const double p0 = sw ? a01 : a00, p1 = sw ? a11 : a01, pr = sw ? r1 : r0;
+            const double q0 = sw ? a00 : a01, q1 = sw ? a01 : a11, qr = sw ? r0 : r1;
+            if (fabs(p0) > 1e-14 * dmax) {
+                // lane 0: det = p0 q1 - q0 p1; lane 1: p0 qr - q0 pr (gamma1 det);
+                // lane 2: pr q1 - p1 qr (gamma0 det), as one x y - z w
+                const double x = lane == 2 ? pr : p0;
+                const double y = lane == 1 ? qr : q1;
+                const double z = lane == 2 ? p1 : q0;
+                const double w = lane == 0 ? p1 : (lane == 1 ? pr : qr);
+                const double t = x * y - z * w;
+                const double det = __shfl_sync(kFull, t, 0);
+                if (fabs(det) > 1e-14 * dmax * fabs(p0)) {
+                    const double gm = t * (1.0 / det);
+                    const double gm1 = __shfl_sync(kFull, gm, 1), gm0 = __shfl_sync(kFull, gm, 2);
+                    const double sum = gm0 + gm1;
+                    if (isfinite(sum)) { c0 = gm0; c1 = gm1; cL = 1.0 - sum; }
+                }
+            }
+        }
+    }
+}
+
+// Coefficient of history column j (0..2, newest last) from anderson3_warp's
+// (c0, c1, cL): n = 2 -> (g0, g1, L) = (0, 1, 2); n = 1 -> (g0, L) = (1, 2).
+__device__ __forceinline__ double anderson3_coef(int j, int n, double c0, double c1, double cL) {
+    return j == 2 ? cL : (n == 2 ? (j == 0 ? c0 : c1) : (n == 1 && j == 1 ? c0 : 0.0));
+}
+
+// The lead warp's update of the depth-3 Gram history G (the leading 3 x 3 of a
+// row length LDG array in shared or global memory, newest last) with the new row (lane k < 3 holds <F_L, F_k>), returning in lane k < 5
+// entry k of (a00, a01, a11, r0, r1) for the window of m columns.
+template <int LDG>
+__device__ __forceinline__ double gram3_update_warp(double (*G)[LDG], double nr, int m) {
+    const int lane = threadIdx.x & 31;
+    const int i = lane / 3, j = lane - 3 * i;
+    const double ni = __shfl_sync(kFull, nr, i < 3 ? i : 0), nj = __shfl_sync(kFull, nr, j);
+    double val = 0.0;
+    if (lane < 9) val = (i < 2 && j < 2) ? G[i + 1][j + 1] : (i == 2 ? nj : ni);
+    __syncwarp();
+    if (lane < 9) G[i][j] = val;
+    __syncwarp();
+    const int L = 2, g0 = 3 - (m < 2 ? 2 : m), g1 = g0 + 1;
+    // a_ij = G_ij - G_iL - G_jL + G_LL and r_i = G_LL - G_iL in one shape
+    const bool isr = lane >= 3;
+    const int gi = (lane == 0 || lane == 1 || lane == 3) ? g0 : g1;
+    const int gj = lane == 0 ? g0 : g1;
+    const double u = isr ? G[L][L] : G[gi][gj];
+    const double w = isr ? 0.0 : G[gj][L];
+    const double z = isr ? 0.0 : G[L][L];
+    return ((u - G[gi][L]) - w) + z;
+}
+
 // Outer least squares on the 2-component scaled residuals (thread 0 only).
 __device__ inline void outer_anderson(const double (&fh)[kMaxOuterMem][2], int m, double* beta) {
     constexpr int MM = kMaxOuterMem;
@@ -195,13 +354,74 @@ __device__ inline void outer_anderson(const double (&fh)[kMaxOuterMem][2], int m
     anderson_solve<MM>(G, m, beta);
 }
 
+// One outer Anderson step of Algorithm 1 (the mixing of the matter iterate,
+// stopped by Algorithm 3), run by all 32 lanes of one warp with every lane
+// holding the node's scalars.  Pushes q = (qv0, qv1) and its residual
+// (q - y) / |y*| (ri_ys = 1 / |y*|) onto the histories qh, fh (newest last;
+// shared or global memory; lane 0 writes) and returns the mixed iterate in
+// every lane.  At depth mo <= 3 the least squares runs lane-parallel
+// (anderson3_warp) on the eliminated normal equations formed from residual
+// differences; deeper windows use outer_anderson.
+__device__ inline void outer_step_warp(double (*qh)[2], double (*fh)[2], double qv0, double qv1, double y0,
+                                       double y1, const double* ri_ys, int mo, double& yn0, double& yn1) {
+    constexpr int MM = kMaxOuterMem;
+    const int ln = threadIdx.x & 31;
+    const double f0 = (qv0 - y0) * ri_ys[0], f1 = (qv1 - y1) * ri_ys[1];
+    __syncwarp();
+    if (ln == 0) {
+        for (int j = 0; j < MM - 1; ++j) {
+            qh[j][0] = qh[j + 1][0]; qh[j][1] = qh[j + 1][1];
+            fh[j][0] = fh[j + 1][0]; fh[j][1] = fh[j + 1][1];
+        }
+        qh[MM - 1][0] = qv0;
+        qh[MM - 1][1] = qv1;
+        fh[MM - 1][0] = f0;
+        fh[MM - 1][1] = f1;
+    }
+    __syncwarp();
+    yn0 = 0.0;
+    yn1 = 0.0;
+    if (mo <= 3) {
+        // lane e < 5: entry e of the eliminated normal equations over the last mo columns,
+        // a_ij = <f_L - f_gi, f_L - f_gj>, r_i = <f_L - f_gi, f_L>
+        const int L = MM - 1, g0 = MM - (mo < 2 ? 2 : mo), g1 = g0 + 1;
+        const bool isr = ln >= 3;
+        const int gi = (ln == 0 || ln == 1 || ln == 3) ? g0 : g1;
+        const int gj = ln == 0 ? g0 : g1;
+        const double u0 = fh[L][0] - fh[gi][0], u1 = fh[L][1] - fh[gi][1];
+        const double w0 = isr ? fh[L][0] : fh[L][0] - fh[gj][0];
+        const double w1 = isr ? fh[L][1] : fh[L][1] - fh[gj][1];
+        double c0, c1, cL;
+        anderson3_warp(u0 * w0 + u1 * w1, mo - 1, c0, c1, cL);
+        for (int j = 3 - mo; j < 3; ++j) {   // history column MM - 3 + j
+            const double b = anderson3_coef(j, mo - 1, c0, c1, cL);
+            yn0 += b * qh[MM - 3 + j][0];
+            yn1 += b * qh[MM - 3 + j][1];
+        }
+    } else {
+        double fl[MM][2], beta[MM];
+        for (int j = 0; j < MM; ++j) { fl[j][0] = fh[j][0]; fl[j][1] = fh[j][1]; }
+        outer_anderson(fl, mo, beta);
+        for (int j = MM - mo; j < MM; ++j) {
+            yn0 += beta[j] * qh[j][0];
+            yn1 += beta[j] * qh[j][1];
+        }
+    }
+}
+
 
 // Node-wide results of the scalar part of ComputeOpacities (shared memory,
 // written by thread 0).
 struct OpacState {
     double eta_e;              // mu_e / T
     double mu[kMaxSpecies];    // neutrino chemical potentials per species
+    double tinv;               // 1 / T
     double tr, tt, ty, kt, ke; // fractional offsets in the table cells
+    double pre[4];             // dtau sc_EmAb, dtau sc_Iso, and the NES and pair prefactors
+    // FP32 copies for the mixed-precision path: mu and 1 / T as double-floats
+    float mu_h[kMaxSpecies], mu_l[kMaxSpecies], tinv_h, tinv_l;
+    float wf[5];               // tr, tt, ty, kt, ke
+    float pre_f[4];
     int ir, it, iy, ikt, ike;  // table cells
 };
 
@@ -231,8 +451,8 @@ struct OpacBufs {
 //    q >= q' and completed by detailed balance, K_Out[q'][q] = a_q / a_q'
 //    K_Out[q][q'] for q' < q (Eqs. inOutInvarianceNES, detailedBalanceNES),
 //    and the pair kernel K_Ann of each particle/antiparticle pair.
-// Thread `lead` does the scalar part and ORs NMC_TABLE_CLAMP into *status when a
-// lookup leaves a table.
+// The warp of thread `lead` (lane 0 of its warp) does the scalar part; `lead`
+// ORs NMC_TABLE_CLAMP into *status when a lookup leaves a table.
 // Ends with the block synchronised.
 template <typename R>
 __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const nmc_params& P, double rho,
@@ -248,55 +468,83 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
     const bool pair_on = (P.proc_mask & NMC_PROC_PAIR) != 0;
     R* fq = b.phi;
 
-    if (tid == lead) {
-        double mu_e, mnu;
-        if (kMixed) {
-            // FP32 root of the electron cubic, then one FP64 Newton step on it (the error
-            // squares): mu_e, and with it D^Eq, must move smoothly with (T, Ye), or the outer
-            // iteration's map is noisy at the 1e-7 level and stalls above tol_outer
-            const EosScaleF es = eos_scale(rho, Ye);
-            const double m0 = eos_mu_e_f(es.ne, (float)T);
-            const double pi2T2 = kPi * kPi * T * T;
-            const double ned = Ye * rho / kMB * (kHbarC * kHbarC * kHbarC);   // FP64 target
-            const double cub = m0 * (m0 * m0 + pi2T2) - 3.0 * kPi * kPi * ned;
-            mu_e = m0 - cub / (3.0 * m0 * m0 + pi2T2);
-            mnu = mu_e - eos_mu_hat(T, Ye);
-        } else {
-            mu_e = eos_mu_e(rho, T, Ye);
-            mnu = mu_e - eos_mu_hat(T, Ye);
+    if ((tid >> 5) == (lead >> 5)) {
+        // The lead warp, every lane carrying the node's scalars: the independent evaluations of one
+        // function (the logarithms, the five table cells) run on different lanes for the cost of
+        // one, since a scalar FP64 step costs the same on 1 or 32 lanes.  Lane 0 writes.
+        const int ln = tid & 31;
+        // log10 of rho, T, 1 - Ye and Ye on lanes 0..3; ln((1 - Ye)/Ye) = ln 10 (log10(1-Ye) - log10 Ye)
+        const double lx = log10(ln == 0 ? rho : (ln == 1 ? T : (ln == 2 ? 1.0 - Ye : Ye)));
+        const double lrho = __shfl_sync(kFull, lx, 0), lT = __shfl_sync(kFull, lx, 1);
+        const double lratio = (__shfl_sync(kFull, lx, 2) - __shfl_sync(kFull, lx, 3)) * kLn10;
+        // mixed: the FP32 root of the electron cubic, then one FP64 Newton step on it (the error
+        // squares): mu_e, and with it D^Eq, must move smoothly with (T, Ye), or the outer
+        // iteration's map is noisy at the 1e-7 level and stalls above tol_outer
+        const double mu_e = kMixed ? eos_mu_e_refined(rho, T, Ye) : eos_mu_e(rho, T, Ye);
+        const double mnu = mu_e - (T * lratio + kDmNP);   // mu_e - mu_hat
+        const double tinv = 1.0 / T;
+        const double eta_e = mu_e / T;
+        // table cells in FP64 in both precisions, lane 0: log10 rho, 1: log10 T (EmAb/Iso axis),
+        // 2: Ye, 3: log10 T (kernel axis), 4: eta_e
+        const int nax = (nes_on || pair_on) ? 5 : 3;
+        const Axis ax = ln == 0 ? tb.rho : (ln == 1 ? tb.t : (ln == 2 ? tb.ye : (ln == 3 ? tb.kt : tb.eta)));
+        int ci = 0, cl = 0;
+        double ct = 0.0;
+        axis_cell<double>(ln == 0 ? lrho : ((ln == 1 || ln == 3) ? lT : (ln == 2 ? Ye : eta_e)), ax, &ci, &ct, &cl);
+        const bool any_cl = __ballot_sync(kFull, cl && ln < nax) != 0u;
+        if (ln == 0) { os->ir = ci; os->tr = ct; }
+        if (ln == 1) { os->it = ci; os->tt = ct; }
+        if (ln == 2) { os->iy = ci; os->ty = ct; }
+        if (ln == 3 && nax == 5) { os->ikt = ci; os->kt = ct; }
+        if (ln == 4 && nax == 5) { os->ike = ci; os->ke = ct; }
+        if (kMixed && ln < nax) os->wf[ln] = (float)ct;
+        if (ln == 0) {
+            os->tinv = tinv;
+            os->eta_e = eta_e;
+            for (int sp = 0; sp < kMaxSpecies; ++sp) os->mu[sp] = sp == 0 ? mnu : (sp == 1 ? -mnu : 0.0);
+            if (any_cl) *status |= NMC_TABLE_CLAMP;
+            const double unit = kMixed ? dtau : dtau * kCW;   // FP32 tables carry 4 pi/(hc)^3
+            os->pre[0] = dtau * sc[0];
+            os->pre[1] = dtau * sc[1];
+            os->pre[2] = unit * sc[2];
+            os->pre[3] = unit * sc[3];
+            if (kMixed) {
+                const F2 m2 = f2_from(mnu), t2 = f2_from(tinv);
+                for (int sp = 0; sp < kMaxSpecies; ++sp) {
+                    os->mu_h[sp] = sp == 0 ? m2.h : (sp == 1 ? -m2.h : 0.f);
+                    os->mu_l[sp] = sp == 0 ? m2.l : (sp == 1 ? -m2.l : 0.f);
+                }
+                os->tinv_h = t2.h;
+                os->tinv_l = t2.l;
+                for (int k = 0; k < 4; ++k) os->pre_f[k] = (float)os->pre[k];
+            }
         }
-        os->eta_e = mu_e / T;
-        for (int sp = 0; sp < kMaxSpecies; ++sp) os->mu[sp] = sp == 0 ? mnu : (sp == 1 ? -mnu : 0.0);
-        int cl = 0;   // table cells in FP64 in both precisions (one thread, a few operations)
-        axis_cell<double>(log10(rho), tb.rho, &os->ir, &os->tr, &cl);
-        axis_cell<double>(log10(T), tb.t, &os->it, &os->tt, &cl);
-        axis_cell<double>(Ye, tb.ye, &os->iy, &os->ty, &cl);
-        if (nes_on || pair_on) {
-            axis_cell<double>(log10(T), tb.kt, &os->ikt, &os->kt, &cl);
-            axis_cell<double>(os->eta_e, tb.eta, &os->ike, &os->ke, &cl);
-        }
-        if (cl) *status |= NMC_TABLE_CLAMP;
     }
     __syncthreads();
     // Fermi--Dirac at the projection quadrature points of every element
     {
         const int nqp = g.n_elem * kProjQuad;
         if (s < NS) {
-            const R mu = (R)os->mu[s], Tinv = (R)(1.0 / T);
-            const double mud = os->mu[s], Tinvd = 1.0 / T;
+            const R mu = (R)os->mu[s], Tinv = (R)os->tinv;
+            const float muh = os->mu_h[s], mul = os->mu_l[s], tih = os->tinv_h, til = os->tinv_l;
             for (int i = q; i < nqp; i += NEP) {
                 if (kMixed) {
                     // f and 1 - f from one exp, each without cancellation.  x = (E - mu)/T reaches
                     // ~100 in the tail, where rounding x to FP32 would move exp(-|x|) by ~1e-5 in
-                    // steps; x is formed in FP64 and split, e^-|x| = expf(-|x_hi|) (1 - |x|_lo)
-                    const double xd = (g.proj_e[i] - mud) * Tinvd;
-                    const double ax = fabs(xd);
-                    const float xh = (float)ax;
-                    const float xl = (float)(ax - (double)xh);
+                    // steps; x is formed as a double-float, e^-|x| = expf(-|x_hi|) (1 - |x|_lo)
+                    float e1, e2;
+                    const float d0 = two_sum(g.proj_e_f[i], -muh, &e1);
+                    const float dh = two_sum(d0, __fadd_rn(e1, __fsub_rn(g.proj_e_fl[i], mul)), &e2);
+                    const float x0 = __fmul_rn(dh, tih);
+                    float x1 = fmaf(dh, tih, -x0);   // dh tih = x0 + x1 exactly
+                    x1 = fmaf(dh, til, x1);
+                    x1 = fmaf(e2, tih, x1);
+                    const bool pos = x0 > 0.f;
+                    const float xh = fabsf(x0), xl = pos ? x1 : -x1;
                     const R t = r_exp(-xh) * (1.0f - xl);
                     const R inv = (R)1 / ((R)1 + t);
-                    fq[s * nqp + i] = xd > 0 ? t * inv : inv;
-                    fq[(NS + s) * nqp + i] = xd > 0 ? inv : t * inv;
+                    fq[s * nqp + i] = pos ? t * inv : inv;
+                    fq[(NS + s) * nqp + i] = pos ? inv : t * inv;
                 } else {
                     fq[s * nqp + i] = (R)1 / (r_exp(((R)g.proj_e[i] - mu) * Tinv) + (R)1);
                 }
@@ -362,7 +610,9 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         const int nr = tb.rho.n, nt = tb.t.n, ny = tb.ye.n;
         const long long base = ((((long long)s * ny + os->iy) * nt + os->it) * nr + os->ir) * NE + q;
         const long long dR = NE, dT = (long long)nr * NE, dY = (long long)nt * nr * NE;
-        const R tr = (R)os->tr, tt = (R)os->tt, ty = (R)os->ty;
+        const R tr = kMixed ? (R)os->wf[0] : (R)os->tr;
+        const R tt = kMixed ? (R)os->wf[1] : (R)os->tt;
+        const R ty = kMixed ? (R)os->wf[2] : (R)os->ty;
         // ln chi as the first corner plus weighted differences: the corners are ~ -20, so an
         // FP32 sum of the corner values themselves would round ln chi by ~2e-6 in steps
         const R le0 = kMixed ? (R)tb.emab_f[base] : (R)tb.emab[base];
@@ -378,19 +628,21 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         }
         le += le0;
         li += li0;
-        chiab = (P.proc_mask & NMC_PROC_EMAB) ? (R)(dtau * sc[0]) * r_exp(le) : (R)0;
-        sig = (P.proc_mask & NMC_PROC_ISO) ? (R)(dtau * sc[1]) * r_exp(li) : (R)0;
+        const R pe = kMixed ? (R)os->pre_f[0] : (R)os->pre[0];
+        const R pi = kMixed ? (R)os->pre_f[1] : (R)os->pre[1];
+        chiab = (P.proc_mask & NMC_PROC_EMAB) ? pe * r_exp(le) : (R)0;
+        sig = (P.proc_mask & NMC_PROC_ISO) ? pi * r_exp(li) : (R)0;
     }
     // NES and pair kernels: bilinear in (log10 T, eta_e), times dtau 4 pi / (hc)^3
     if (nes_on || pair_on) {
-        const R kt = (R)os->kt, ke = (R)os->ke;
+        const R kt = kMixed ? (R)os->wf[3] : (R)os->kt;
+        const R ke = kMixed ? (R)os->wf[4] : (R)os->ke;
         const R w00 = ((R)1 - kt) * ((R)1 - ke), w10 = kt * ((R)1 - ke);
         const R w01 = ((R)1 - kt) * ke, w11 = kt * ke;
         const long long mat = (long long)NE * NE;
         const long long sE = mat, sT = (long long)tb.eta.n * mat;
-        const double unit = kMixed ? dtau : dtau * kCW;   // FP32 tables carry 4 pi/(hc)^3
         if (nes_on && s < NS) {
-            const R c = (R)(unit * sc[2]);
+            const R c = kMixed ? (R)os->pre_f[2] : (R)os->pre[2];
             const long long off = (((long long)s * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
             R* P0 = b.phi + s * NE * LD;
             // lower triangle incl. diagonal, entries enumerated row by row so that every lane of the
@@ -415,7 +667,7 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         }
         if (pair_on && s < NS) {
             const int pr = s >> 1;
-            const R c = (R)(unit * sc[3]);
+            const R c = kMixed ? (R)os->pre_f[3] : (R)os->pre[3];
             const long long off = (((long long)pr * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
             R* A0 = b.ann + pr * NE * LD;
             for (int idx = (s & 1) * NEP + q; idx < NE * NE; idx += 2 * NEP) {

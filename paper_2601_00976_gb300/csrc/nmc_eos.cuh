@@ -24,11 +24,11 @@ __device__ __forceinline__ double eos_mu_e(double rho, double T, double Ye) {
     return -2.0 * sqrt(p / 3.0) * sinh(asinh(1.5 * q / p * sqrt(3.0 / p)) / 3.0);
 }
 
-// eps(rho, T, Ye) in erg/g and d eps / dT at fixed rho, Ye.
-__device__ __forceinline__ void eos_eps(double rho, double T, double Ye, double* eps, double* deps) {
+// eps(rho, T, Ye) in erg/g and d eps / dT at fixed rho, Ye, given the electron
+// chemical potential mu at (rho, T, Ye).
+__device__ __forceinline__ void eos_eps_at_mu(double rho, double T, double mu, double* eps, double* deps) {
     const double pi2 = kPi * kPi;
     const double hc3 = kHbarC * kHbarC * kHbarC;
-    const double mu = eos_mu_e(rho, T, Ye);
     const double T2 = T * T, mu2 = mu * mu;
     const double ue = (7.0 * pi2 * T2 * T2 / 60.0 + 0.5 * T2 * mu2 + mu2 * mu2 / (4.0 * pi2)) / hc3;
     const double nb = rho / kMB;
@@ -39,6 +39,10 @@ __device__ __forceinline__ void eos_eps(double rho, double T, double Ye, double*
     const double dmu = -2.0 * pi2 * T * mu / (3.0 * mu2 + pi2 * T2);
     const double due = (7.0 * pi2 * T2 * T / 15.0 + T * mu2 + (T2 * mu + mu2 * mu / pi2) * dmu) / hc3;
     *deps = (due + 1.5 * nb + 4.0 * pi2 / 15.0 * T2 * T / hc3) * f;
+}
+
+__device__ __forceinline__ void eos_eps(double rho, double T, double Ye, double* eps, double* deps) {
+    eos_eps_at_mu(rho, T, eos_mu_e(rho, T, Ye), eps, deps);
 }
 
 // T with eps(rho, T, Ye) = eps_t: safeguarded Newton in T within [kTMin, kTMax].
@@ -84,10 +88,6 @@ __device__ __forceinline__ double eos_deps_dye(double rho, double T, double Ye) 
     return kMeVErg / kMB * 3.0 * mu * (mu2 + pi2 * T2) / (3.0 * mu2 + pi2 * T2);
 }
 
-__device__ __forceinline__ double eos_mu_hat(double T, double Ye) {
-    return T * log((1.0 - Ye) / Ye) + kDmNP;
-}
-
 // ---- FP32 variants for the mixed-precision path ----
 // Densities are carried times (hbar c)^3 (MeV^3) and energy densities times
 // (hbar c)^3 (MeV^4), so every intermediate stays inside FP32 range:
@@ -116,6 +116,19 @@ __device__ __forceinline__ float eos_mu_e_f(float ne, float T) {
     return -2.0f * sqrtf(p / 3.0f) * sinhf(asinhf(1.5f * q / p * sqrtf(3.0f / p)) / 3.0f);
 }
 
+// mu_e in FP64 for the mixed path: the FP32 root of the electron cubic
+// x^3 + pi^2 T^2 x - 3 pi^2 n_e (hbar c)^3 = 0 and one FP64 Newton step on it,
+// which squares its relative error (~1e-7 to ~1e-14) for a handful of FP64
+// operations instead of the closed form's FP64 asinh and sinh.
+__device__ __forceinline__ double eos_mu_e_refined(double rho, double T, double Ye) {
+    const EosScaleF es = eos_scale(rho, Ye);
+    const double m0 = eos_mu_e_f(es.ne, (float)T);
+    const double pi2T2 = kPi * kPi * T * T;
+    const double ned = Ye * rho / kMB * (kHbarC * kHbarC * kHbarC);   // FP64 target
+    const double cub = m0 * (m0 * m0 + pi2T2) - 3.0 * kPi * kPi * ned;
+    return m0 - cub / (3.0 * m0 * m0 + pi2T2);
+}
+
 __device__ __forceinline__ void eos_u_f(const EosScaleF& sc, float T, float* u, float* du) {
     const float pi2 = (float)(kPi * kPi);
     const float mu = eos_mu_e_f(sc.ne, T);
@@ -128,7 +141,8 @@ __device__ __forceinline__ void eos_u_f(const EosScaleF& sc, float T, float* u, 
 }
 
 // Temperature for the mixed path: bracketed Newton in FP32 to ~1e-7, then one
-// FP64 Newton step on eps(rho, T, Ye), which squares the relative error.
+// FP64 Newton step on eps(rho, T, Ye) (with mu_e refined from its FP32 root),
+// which squares the relative error.
 __device__ inline double eos_temperature_mixed(double rho, double eps_t, double Ye, double T0, bool* ok) {
     *ok = true;
     if (!(Ye > 0.0 && Ye < 1.0) || !isfinite(eps_t)) {
@@ -155,7 +169,7 @@ __device__ inline double eos_temperature_mixed(double rho, double eps_t, double 
         if (d <= 2e-7f * T || hi - lo <= 4e-7f * hi) break;
     }
     double Td = T, e, de;
-    eos_eps(rho, Td, Ye, &e, &de);
+    eos_eps_at_mu(rho, Td, eos_mu_e_refined(rho, Td, Ye), &e, &de);
     const double Tn = Td - (e - eps_t) / de;
     return (Tn > kTMin && Tn < kTMax) ? Tn : Td;
 }

@@ -65,18 +65,20 @@ struct NodeShared {
     double rho, dtau, T;
     double sc[4];
     double y[2], ystar[2], qv[2];
+    double k_eps, k_ye, ri_ys[2];
     double EN_star[2];
     double qh[kMaxOuterMem][2], fh[kMaxOuterMem][2];
     double G[MAXM][MAXM];
     double alpha[MAXM];
     float alpha_f[MAXM];
-    double dnorm[kMaxSpecies];
+    double thr[2][kMaxSpecies];   // Algorithm 2 thresholds on the D and I changes (FP64 path)
+    float thr_f[2][kMaxSpecies];  // the same rounded to FP32 (mixed path)
     double sp_out[kMaxSpecies * 4];
     double blk_out[8];
     OpacState op;
     long long node;
     int status, n_inner, n_outer;
-    int conv_in, conv_out, bad, done;
+    int conv_out, bad, done;
 };
 
 }  // namespace
@@ -116,11 +118,13 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
     const double W3q = act ? g.w3[q] : 0.0;
     const R Wt = act ? (kMixed ? (R)g.wt_f[q] : (R)g.wt[q]) : (R)0;
 
-    // Mixed precision keeps the number moment D in FP64 (near a fixed point where
-    // 1 + dtau chi ~ 1e4, FP32 increments of D fall below one ulp long before the
-    // equation residual is small) and its Anderson history Qh[.][0] as FP32
-    // offsets Q_j - D from the current iterate, which are small near convergence:
-    // the mixing then costs one FP64 add instead of FP64 arithmetic on the window.
+    // Mixed precision keeps the number moment D as a double-float (near a fixed
+    // point where 1 + dtau chi ~ 1e4, FP32 increments of D fall below one ulp long
+    // before the equation residual is small) and its Anderson history Qh[.][0] as
+    // FP32 offsets Q_j - D from the current iterate, which are small near
+    // convergence: the mixing then costs one double-float add.  A warp's FP64
+    // instruction holds its SMSP's FP64 pipe ~64 cycles, so the inner loop issues
+    // none per thread; only the lead warp's least squares stays in FP64.
     R Fh[MAXM][4], Qh[MAXM][4];
 #pragma unroll
     for (int j = 0; j < MAXM; ++j) {
@@ -163,6 +167,12 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
             if (okin) eos_eps(rho, T, Ye, &e, &de);
             nd->ystar[0] = e;
             nd->ystar[1] = Ye;
+            // per-node factors of the matter update: eps and Ye per unit change of the neutrino
+            // energy and lepton number densities, and the outer residuals' scales 1 / |y*|
+            nd->k_eps = kMeVErg / rho;
+            nd->k_ye = kMB / rho;
+            nd->ri_ys[0] = 1.0 / fabs(e);
+            nd->ri_ys[1] = 1.0 / fabs(Ye);
             nd->y[0] = e;
             nd->y[1] = Ye;
             nd->n_inner = 0;
@@ -196,9 +206,9 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         const R Ds = (R)Dsd;
         const R Is[3] = {(R)Isd[0], (R)Isd[1], (R)Isd[2]};
         R M[4] = {Ds, Is[0], Is[1], Is[2]};
-        double Dd = Dsd;   // FP64 number moment (mixed precision); M[0] is its FP32 shadow
-        // mixed: per outer iteration, numerator W~ (D* - D) + W~ dtau chi_EmAb (D^Eq - D) = A0 - c12 D
-        double A0 = 0.0, c12 = 0.0, deq_d = 0.0;
+        // mixed: the number moment as a double-float (M[0] is its high word), and per outer
+        // iteration the numerator W~ (D* - D) + W~ dtau chi_EmAb (D^Eq - D) = A0 - c12 D
+        F2 Dx = f2_from(Dsd), A0x = {0.f, 0.f}, c12x = {0.f, 0.f};
         R chiab = 0, sig = 0, deq = 0, deqc = 0;
         int outer_exit = 0;
 
@@ -207,10 +217,9 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
             compute_opacities<R>(g, a.tb, P, nd->rho, nd->T, nd->y[1], nd->dtau, nd->sc, ob, &nd->op,
                                  &nd->status, chiab, sig, deq, deqc, lead);
             if constexpr (kMixed) {
-                deq_d = (double)deq;
                 const double c1 = (double)Wt, c2 = c1 * (double)chiab;
-                A0 = c1 * Dsd + c2 * deq_d;
-                c12 = c1 + c2;
+                A0x = f2_from(c1 * Dsd + c2 * (double)deq);
+                c12x = f2_from(c1 + c2);
             }
             // reference norm ||D^[k,1]||_W per species (Algorithm 2 input)
             {
@@ -219,21 +228,41 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                 species_sum<1, R>(v, red, out, NEP, NS);
                 if (tid == lead) {
                     const double fl = P.norm_floor * sqrt(g.sum_wt);
-                    for (int sp = 0; sp < NS; ++sp) nd->dnorm[sp] = fmax((double)r_sqrt(out[sp]), fl);
+                    // mixed precision: D is a double-float iterate held to tol_inner; the first
+                    // moments are FP32 values, checked against FP32 resolution at the finest
+                    const double tol_i = kMixed ? fmax(P.tol_inner, kFp32Resolution) : P.tol_inner;
+                    for (int sp = 0; sp < NS; ++sp) {
+                        const double dn = fmax((double)r_sqrt(out[sp]), fl);
+                        nd->thr[0][sp] = P.tol_inner * dn;
+                        nd->thr[1][sp] = tol_i * dn;
+                        nd->thr_f[0][sp] = (float)(P.tol_inner * dn);
+                        nd->thr_f[1][sp] = (float)(tol_i * dn);
+                    }
                 }
             }
-            // ================= inner loop =================
-            for (int ell = 1;; ++ell) {
+            // The vectors every bin's contractions read: W~ D, W~ (1 - D), a W~ (1 - D) and (mixed)
+            // the deviation w.  Mixed: the blocking factor 1 - D and the deviation D - D^Eq are
+            // formed from both words of D (1 - D in FP32 has no digits left at D ~ 1 - 1e-6);
+            // 1 - D.h, and D.h - D^Eq near equilibrium, are exact.
+            auto publish = [&](R D32, F2 D2) {
                 if (act) {
-                    // mixed: the blocking factor 1 - D and the deviation D - D^Eq are formed from
-                    // the FP64 D (1 - D in FP32 has no digits left at D ~ 1 - 1e-6)
-                    const R hole = kMixed ? (R)(1.0 - Dd) : (R)1 - M[0];
-                    vWD[sq] = Wt * M[0];
+                    const R hole = kMixed ? (R)__fsub_rn(__fsub_rn(1.0f, D2.h), D2.l) : (R)1 - D32;
+                    vWD[sq] = Wt * D32;
                     vW1D[sq] = Wt * hole;
                     vAW1D[sq] = vA[sq] * Wt * hole;
-                    if constexpr (kMixed) vWdev[sq] = (R)(Dd - deq_d) * (Wt / deqc);
+                    if constexpr (kMixed)
+                        vWdev[sq] = __fadd_rn(__fsub_rn(D2.h, (float)deq), D2.l) * (Wt / deqc);
                 }
-                __syncthreads();
+            };
+            publish(M[0], Dx);
+            __syncthreads();
+            bool inner_stop = false;   // the inner loop hit its cap or a non-finite moment
+            // ================= inner loop =================
+            // Three barriers an iteration: the Gram row's warp partials, the least-squares
+            // coefficients, and the convergence vote.  The next iterate's vectors are written once
+            // the coefficients are out (no thread reads the old ones after that) and the vote's
+            // barrier publishes them.
+            for (int ell = 1;; ++ell) {
                 R F[4] = {0, 0, 0, 0}, Qv[4] = {0, 0, 0, 0};
                 R dlt = 0;         // mixed: Q_D - D, formed without cancellation
                 if (act) {
@@ -306,12 +335,12 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         // the same map written as Q_D = D + W~ (D* - D + dtau C) / (W~ (1 + dtau chi)),
                         // with the net collision term W~ dtau C = W~ dtau chi_EmAb (D^Eq - D) + net NES
                         // + net pair exchanges.  The numerator, whose zero is the fixed point, is
-                        // summed in FP64 around the FP64 D; the denominator only scales the step, so
-                        // FP32 rounding in chi does not move the fixed point.  The history holds
-                        // Q_D - D (the offset of the map value from the current iterate).
-                        const double numW = fma(-c12, Dd, A0) + (double)(cn + cp);
+                        // summed in double-float around the double-float D; the denominator only
+                        // scales the step, so FP32 rounding in chi does not move the fixed point.
+                        // The history holds Q_D - D (the offset of the map value from the iterate).
+                        const R numW = f2_residual(A0x, c12x, Dx, cn + cp);
                         const R inv = (R)1 / ((R)1 + chi);
-                        dlt = (R)numW * (inv / Wt);
+                        dlt = numW * (inv / Wt);
                         Qv[0] = dlt;
                     }
                     R fI;
@@ -338,14 +367,65 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) { Fh[MAXM - 1][c] = F[c]; Qh[MAXM - 1][c] = Qv[c]; }
                 const int m = ell < P.m_inner ? ell : P.m_inner;
-                {   // new row of the Gram matrix; least squares in FP64 (thread 0)
+                if constexpr (MAXM == 3) {
+                    // Least squares in FP64 by the lead warp (anderson3_warp), lane k adding the warps'
+                    // partials of entry k.  FP64: the new Gram row, kept in the history G.  Mixed: the
+                    // block sums are the eliminated normal equations themselves, from FP32 differences
+                    // dF_i = F_L - F_gi (no FP64 formation, no history, no cancellation between Gram
+                    // entries).  The fit covers all four moments, as Algorithm 1 does; fitted to the
+                    // number moments alone, it kept extrapolating once their residual reached the FP32
+                    // noise of the exchange sums and some nodes cycled above tol_inner.
+                    constexpr int K = kMixed ? 5 : 3;
+                    R v[K];
+                    if constexpr (kMixed) {
+                        R d0[4], d1[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            d0[c] = F[c] - (m >= 3 ? Fh[0][c] : Fh[1][c]);
+                            d1[c] = F[c] - Fh[1][c];
+                        }
+                        v[0] = d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2] + d0[3] * d0[3];
+                        v[1] = d0[0] * d1[0] + d0[1] * d1[1] + d0[2] * d1[2] + d0[3] * d1[3];
+                        v[2] = d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2] + d1[3] * d1[3];
+                        v[3] = d0[0] * F[0] + d0[1] * F[1] + d0[2] * F[2] + d0[3] * F[3];
+                        v[4] = d1[0] * F[0] + d1[1] * F[1] + d1[2] * F[2] + d1[3] * F[3];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            v[j] = F[0] * Fh[j][0] + F[1] * Fh[j][1] + F[2] * Fh[j][2] + F[3] * Fh[j][3];
+                    }
+                    warp_partials<K, R>(v, red);
+                    __syncthreads();
+                    if ((tid >> 5) == (lead >> 5)) {
+                        const int k = tid & 31;
+                        const R* pr = reinterpret_cast<const R*>(red);
+                        R sk = 0;
+                        if (k < K)
+                            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sk += pr[i * K + k];
+                        double e;
+                        if constexpr (kMixed) e = (double)sk;
+                        else e = gram3_update_warp<3>(nd->G, sk, m);
+                        double c0, c1, cL;
+                        anderson3_warp(e, m - 1, c0, c1, cL);
+                        if (k < 3) {
+                            const double a = anderson3_coef(k, m - 1, c0, c1, cL);
+                            nd->alpha[k] = a;
+                            nd->alpha_f[k] = (float)a;
+                        }
+                    }
+                    __syncthreads();
+                } else {   // new row of the Gram matrix; the lead adds the warps' partials and solves
+                           // the least squares in FP64
                     R v[MAXM];
 #pragma unroll
-                    for (int j = 0; j < MAXM; ++j)
+                    for (int j = 0; j < MAXM; ++j) {
                         v[j] = F[0] * Fh[j][0] + F[1] * Fh[j][1] + F[2] * Fh[j][2] + F[3] * Fh[j][3];
-                    R* out = reinterpret_cast<R*>(nd->blk_out);
-                    block_sum<MAXM, R>(v, red, out);
+                    }
+                    warp_partials<MAXM, R>(v, red);
+                    __syncthreads();
                     if (tid == lead) {
+                        R out[MAXM];
+                        sum_partials<MAXM, R>(red, out);
                         for (int i = 0; i < MAXM - 1; ++i)
                             for (int j = 0; j < MAXM - 1; ++j) nd->G[i][j] = nd->G[i + 1][j + 1];
                         for (int j = 0; j < MAXM; ++j) {
@@ -359,7 +439,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                 }
                 R Mn[4];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = kMixed ? 1 : 0; c < 4; ++c) {   // mixed: D below, in offset form
                     R acc = 0;
 #pragma unroll
                     for (int j = 0; j < MAXM; ++j)
@@ -367,7 +447,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                             acc = r_fma(kMixed ? (R)nd->alpha_f[j] : (R)nd->alpha[j], Qh[j][c], acc);
                     Mn[c] = act ? acc : (R)0;
                 }
-                double Ddn = Dd;
+                F2 Dxn = Dx;
                 R sD = 0;   // mixed: D^new - D
                 if constexpr (kMixed) {
                     // in difference form, o_L + sum_j alpha_j (o_j - o_L) with o = Q - D: the
@@ -377,9 +457,11 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                     for (int j = 0; j < MAXM - 1; ++j)
                         if (j >= MAXM - m) acc = r_fma((R)nd->alpha_f[j], Qh[j][0] - Qh[MAXM - 1][0], acc);
                     sD = act ? acc : (R)0;
-                    Ddn = Dd + (double)sD;
-                    Mn[0] = (R)Ddn;
+                    Dxn = f2_add(Dx, sD);
+                    Mn[0] = Dxn.h;
                 }
+                publish(Mn[0], Dxn);
+                int vote = 1;
                 {   // Algorithm 2: per species, W-weighted squares of the change per moment
                     R v[4];
 #pragma unroll
@@ -388,80 +470,89 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                     if (act && !(isfinite(Mn[0]) && isfinite(Mn[1]) && isfinite(Mn[2]) && isfinite(Mn[3]) &&
                                  isfinite(sD)))
                         nd->bad = 1;
-                    R* out = reinterpret_cast<R*>(nd->sp_out);
-                    species_sum<4, R>(v, red, out, NEP, NS);
-                    if (tid == lead) {
-                        int conv = 1;
-                        // mixed precision: D is an FP64 iterate and is held to tol_inner; the first
-                        // moments are FP32 values, checked against FP32 resolution at the finest
-                        const double tol_i = kMixed ? fmax(P.tol_inner, kFp32Resolution) : P.tol_inner;
-                        for (int sp = 0; sp < NS; ++sp) {
-                            R mx = out[sp * 4 + 1];
-                            for (int c = 2; c < 4; ++c) mx = fmax(mx, out[sp * 4 + c]);
-                            if (!(r_sqrt(out[sp * 4]) <= (R)(P.tol_inner * nd->dnorm[sp]))) conv = 0;
-                            if (!(r_sqrt(mx) <= (R)(tol_i * nd->dnorm[sp]))) conv = 0;
+                    auto species_ok = [&](const R* u, int sp) -> int {
+                        R mx = u[1];
+                        for (int c = 2; c < 4; ++c) mx = fmax(mx, u[c]);
+                        if constexpr (kMixed)
+                            return r_sqrt(u[0]) <= nd->thr_f[0][sp] && r_sqrt(mx) <= nd->thr_f[1][sp];
+                        else
+                            return r_sqrt(u[0]) <= nd->thr[0][sp] && r_sqrt(mx) <= nd->thr[1][sp];
+                    };
+                    if (NEP <= 32) {
+                        // a species group lies inside one warp: its sums are formed in registers
+                        // (the butterfly leaves the same sum in every lane of the group) and each
+                        // lane votes for its own species
+                        for (int off = NEP >> 1; off > 0; off >>= 1) {
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) v[c] += __shfl_xor_sync(kFull, v[c], off);
                         }
-                        nd->n_inner += 1;
-                        if (nd->bad) nd->status |= NMC_NONFINITE;
-                        if (!conv && !nd->bad && ell >= P.max_inner) nd->status |= NMC_NOT_CONVERGED_INNER;
-                        nd->conv_in = conv || nd->bad || ell >= P.max_inner;
+                        if (s < NS) vote = species_ok(v, s);
+                    } else {
+                        R* out = reinterpret_cast<R*>(nd->sp_out);
+                        species_sum<4, R>(v, red, out, NEP, NS);
+                        for (int sp = 0; sp < NS; ++sp) vote &= species_ok(out + sp * 4, sp);
                     }
-                    __syncthreads();
+                }
+                const bool conv = __syncthreads_and(vote) != 0;
+                const bool bad = *reinterpret_cast<volatile int*>(&nd->bad) != 0;
+                const bool capped = !conv && !bad && ell >= P.max_inner;
+                if (tid == lead) {
+                    nd->n_inner += 1;
+                    if (bad) nd->status |= NMC_NONFINITE;
+                    if (capped) nd->status |= NMC_NOT_CONVERGED_INNER;
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) M[c] = Mn[c];
-                Dd = Ddn;
+                Dx = Dxn;
                 if constexpr (kMixed) {   // offsets now relative to the new iterate
 #pragma unroll
                     for (int j = 0; j < MAXM; ++j) Qh[j][0] -= sD;
                 }
-                if (nd->conv_in) break;
+                if (conv || bad || ell >= P.max_inner) {
+                    inner_stop = bad || capped;
+                    break;
+                }
             }
             // an inner loop stopped at its cap (or a non-finite moment) ends the node
-            if (P.frozen_matter || nd->bad || (nd->status & NMC_NOT_CONVERGED_INNER)) { outer_exit = 1; }
+            if (P.frozen_matter || inner_stop) outer_exit = 1;
             // ================= matter update (Eq. implicitFluidNodal), FP64 =================
             if (!outer_exit) {
-                const double Dcur = kMixed ? Dd : (double)M[0];
+                const double Dcur = kMixed ? f2_to(Dx) : (double)M[0];
                 double v[2] = {W3q * Dcur, gs * W2q * Dcur};
                 block_sum<2, double>(v, red, nd->blk_out);
-                if (tid == lead) {
+                if ((tid >> 5) == (lead >> 5)) {
+                    // The lead warp, every lane carrying the node's scalars: a scalar FP64 step costs
+                    // the same on 1 or 32 lanes, and the outer least squares runs lane-parallel.
+                    // Lane 0 writes the shared state.
+                    const int ln = tid & 31;
                     const double rho = nd->rho;
-                    const double qv0 = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * kMeVErg / rho;
-                    const double qv1 = nd->ystar[1] - kMB * (nd->blk_out[1] - nd->EN_star[1]) / rho;
-                    nd->qv[0] = qv0;
-                    nd->qv[1] = qv1;
-                    // outer Anderson on residuals scaled by |y*|
-                    for (int j = 0; j < kMaxOuterMem - 1; ++j) {
-                        nd->qh[j][0] = nd->qh[j + 1][0]; nd->qh[j][1] = nd->qh[j + 1][1];
-                        nd->fh[j][0] = nd->fh[j + 1][0]; nd->fh[j][1] = nd->fh[j + 1][1];
-                    }
-                    nd->qh[kMaxOuterMem - 1][0] = qv0;
-                    nd->qh[kMaxOuterMem - 1][1] = qv1;
-                    nd->fh[kMaxOuterMem - 1][0] = (qv0 - nd->y[0]) / fabs(nd->ystar[0]);
-                    nd->fh[kMaxOuterMem - 1][1] = (qv1 - nd->y[1]) / fabs(nd->ystar[1]);
+                    const double qv0 = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * nd->k_eps;
+                    const double qv1 = nd->ystar[1] - (nd->blk_out[1] - nd->EN_star[1]) * nd->k_ye;
+                    const double y0 = nd->y[0], y1 = nd->y[1];
+                    if (ln == 0) { nd->qv[0] = qv0; nd->qv[1] = qv1; }
                     const int mo = k < P.m_outer ? k : P.m_outer;
-                    double beta[kMaxOuterMem];
-                    outer_anderson(nd->fh, mo, beta);
-                    double yn0 = 0.0, yn1 = 0.0;
-                    for (int j = kMaxOuterMem - mo; j < kMaxOuterMem; ++j) {
-                        yn0 += beta[j] * nd->qh[j][0];
-                        yn1 += beta[j] * nd->qh[j][1];
-                    }
-                    const int conv = fabs(yn0 - nd->y[0]) <= P.tol_outer * fabs(nd->ystar[0]) &&
-                                     fabs(yn1 - nd->y[1]) <= P.tol_outer * fabs(nd->ystar[1]);   // Algorithm 3
-                    nd->y[0] = yn0;
-                    nd->y[1] = yn1;
-                    int stop = conv;
-                    if (!(isfinite(yn0) && isfinite(yn1))) { nd->status |= NMC_NONFINITE; stop = 1; }
-                    if (!stop && k >= P.max_outer) { nd->status |= NMC_NOT_CONVERGED_OUTER; stop = 1; }
+                    double yn0, yn1;
+                    outer_step_warp(nd->qh, nd->fh, qv0, qv1, y0, y1, nd->ri_ys, mo, yn0, yn1);
+                    const int conv = fabs(yn0 - y0) <= P.tol_outer * fabs(nd->ystar[0]) &&
+                                     fabs(yn1 - y1) <= P.tol_outer * fabs(nd->ystar[1]);   // Algorithm 3
+                    int stop = conv, st = 0;
+                    double Tn = nd->T;
+                    if (!(isfinite(yn0) && isfinite(yn1))) { st |= NMC_NONFINITE; stop = 1; }
+                    if (!stop && k >= P.max_outer) { st |= NMC_NOT_CONVERGED_OUTER; stop = 1; }
                     if (!stop) {   // an iterate outside the EoS domain stops the node
                         bool ok;
-                        const double Tn = kMixed ? eos_temperature_mixed(rho, yn0, yn1, nd->T, &ok)
-                                                 : eos_temperature(rho, yn0, yn1, nd->T, &ok);
-                        if (ok) nd->T = Tn;
-                        else { nd->status |= NMC_EOS_FAIL; stop = 1; }
+                        const double Tk = kMixed ? eos_temperature_mixed(rho, yn0, yn1, Tn, &ok)
+                                                 : eos_temperature(rho, yn0, yn1, Tn, &ok);
+                        if (ok) Tn = Tk;
+                        else { st |= NMC_EOS_FAIL; stop = 1; }
                     }
-                    nd->conv_out = stop;
+                    if (ln == 0) {
+                        nd->y[0] = yn0;
+                        nd->y[1] = yn1;
+                        nd->T = Tn;
+                        nd->status |= st;
+                        nd->conv_out = stop;
+                    }
                 }
                 __syncthreads();
                 if (nd->conv_out) outer_exit = 1;
@@ -473,12 +564,12 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         }
         // ================= finalize =================
         {   // q(M, y) at the final moments (Eq. implicitFluidNodal), FP64
-            const double Dcur = kMixed ? Dd : (double)M[0];
+            const double Dcur = kMixed ? f2_to(Dx) : (double)M[0];
             double v[2] = {W3q * Dcur, gs * W2q * Dcur};
             block_sum<2, double>(v, red, nd->blk_out);
             if (tid == lead) {
-                nd->qv[0] = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * kMeVErg / nd->rho;
-                nd->qv[1] = nd->ystar[1] - kMB * (nd->blk_out[1] - nd->EN_star[1]) / nd->rho;
+                nd->qv[0] = nd->ystar[0] - (nd->blk_out[0] - nd->EN_star[0]) * nd->k_eps;
+                nd->qv[1] = nd->ystar[1] - (nd->blk_out[1] - nd->EN_star[1]) * nd->k_ye;
             }
         }
         if (tid == lead) {
@@ -505,7 +596,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         }
         if (act) {
             const long long o = (n * NS + s) * NE + q;
-            a.J_out[o] = kMixed ? Dd : (double)M[0];
+            a.J_out[o] = kMixed ? f2_to(Dx) : (double)M[0];
             a.H_out[o * 3 + 0] = (double)M[1];
             a.H_out[o * 3 + 1] = (double)M[2];
             a.H_out[o * 3 + 2] = (double)M[3];

@@ -28,6 +28,7 @@ constexpr double kHbarC = kHC / (2.0 * kPi);       // MeV cm
 constexpr double kMB = 1.66053906660e-24;          // g (average baryon mass)
 constexpr double kMeVErg = 1.602176634e-6;         // erg/MeV
 constexpr double kDmNP = 1.2933;                   // MeV
+constexpr double kLn10 = 2.302585092994045684;     // ln 10
 constexpr double kTMin = 1.0e-3;                   // MeV, EoS range
 constexpr double kTMax = 1.0e3;
 constexpr double kCW = 4.0 * kPi / (kHC * kHC * kHC);   // 4 pi / (hc)^3  [cm^-3 MeV^-3]
@@ -50,7 +51,8 @@ struct DevGrid {
     const double* proj_a;  // [n_elem][Q] eps^2-weighted cell-average weights
     const double* wt;      // [ne] W2 / (4 pi / (hc)^3) = w eps^2 Delta eps  [MeV^3]
     // FP32 copies for the mixed-precision kernel
-    const float* proj_e_f;
+    const float* proj_e_f;   // proj_e as double-floats: high words
+    const float* proj_e_fl;  //                          low words
     const float* proj_c_f;
     const float* proj_a_f;
     const float* wt_f;

@@ -40,6 +40,7 @@ struct PlainNode {
     double rho, dtau, T;
     double sc[4];
     double y[2], ystar[2], EN_star[2];
+    double k_eps, k_ye, ri_ys[2];   // matter-update factors and 1 / |y*|, as the fused kernel
     double dnorm[kMaxSpecies];
     double G[kPlainMaxM][kPlainMaxM];
     double qh[kMaxOuterMem][2], fh[kMaxOuterMem][2];
@@ -112,6 +113,10 @@ __global__ void __launch_bounds__(512) plain_setup_kernel(const SolveArgs a, Pla
             if (okin) eos_eps(rho, T, Ye, &e, &de);
             nd->ystar[0] = nd->y[0] = e;
             nd->ystar[1] = nd->y[1] = Ye;
+            nd->k_eps = kMeVErg / rho;
+            nd->k_ye = kMB / rho;
+            nd->ri_ys[0] = 1.0 / fabs(e);
+            nd->ri_ys[1] = 1.0 / fabs(Ye);
             nd->EN_star[0] = out2[0];
             nd->EN_star[1] = out2[1];
             nd->status = okin ? 0 : NMC_BAD_INPUT;
@@ -310,12 +315,19 @@ __global__ void __launch_bounds__(512) plain_inner_kernel(const SolveArgs a, Pla
                     st.qh[h] = Qh[j][c];
                 }
         const int m = ell < P.m_inner ? ell : P.m_inner;
-        {   // new row of the Gram matrix; least squares in FP64 (thread 0)
+        {   // new row of the Gram matrix; least squares in FP64 (warp 0 at depth 3, as the fused
+            // kernel; thread 0 otherwise)
             double v[MAXM];
             for (int j = 0; j < MAXM; ++j)
                 v[j] = F[0] * Fh[j][0] + F[1] * Fh[j][1] + F[2] * Fh[j][2] + F[3] * Fh[j][3];
             block_sum<MAXM, double>(v, red, sh->blk_out);
-            if (tid == 0) {
+            if (MAXM == 3 && tid < 32) {
+                const double nr = tid < 3 ? sh->blk_out[tid] : 0.0;
+                const double e = gram3_update_warp<kPlainMaxM>(nd->G, nr, m);
+                double c0, c1, cL;
+                anderson3_warp(e, m - 1, c0, c1, cL);
+                if (tid < 3) sh->alpha[tid] = anderson3_coef(tid, m - 1, c0, c1, cL);
+            } else if (MAXM != 3 && tid == 0) {
                 double G[MAXM][MAXM];
                 for (int i = 0; i < MAXM - 1; ++i)
                     for (int j = 0; j < MAXM - 1; ++j) G[i][j] = nd->G[i + 1][j + 1];
@@ -381,47 +393,38 @@ __global__ void __launch_bounds__(512) plain_matter_kernel(const SolveArgs a, Pl
         const double D = act ? a.J_out[(n * NS + s) * NE + q] : 0.0;
         double v[2] = {act ? g.w3[q] * D : 0.0, act ? gs * g.w2[q] * D : 0.0};
         block_sum<2, double>(v, red, out2);
-        if (tid == 0) {
+        if (tid < 32) {   // warp 0, every lane carrying the node's scalars (as the fused kernel)
             const int k = nd->k;
             if (stop_now) {
-                nd->n_outer = k;
+                if (tid == 0) nd->n_outer = k;
             } else {
                 const double rho = nd->rho;
-                const double qv0 = nd->ystar[0] - (out2[0] - nd->EN_star[0]) * kMeVErg / rho;
-                const double qv1 = nd->ystar[1] - kMB * (out2[1] - nd->EN_star[1]) / rho;
-                for (int j = 0; j < kMaxOuterMem - 1; ++j) {
-                    nd->qh[j][0] = nd->qh[j + 1][0]; nd->qh[j][1] = nd->qh[j + 1][1];
-                    nd->fh[j][0] = nd->fh[j + 1][0]; nd->fh[j][1] = nd->fh[j + 1][1];
-                }
-                nd->qh[kMaxOuterMem - 1][0] = qv0;
-                nd->qh[kMaxOuterMem - 1][1] = qv1;
-                nd->fh[kMaxOuterMem - 1][0] = (qv0 - nd->y[0]) / fabs(nd->ystar[0]);
-                nd->fh[kMaxOuterMem - 1][1] = (qv1 - nd->y[1]) / fabs(nd->ystar[1]);
+                const double qv0 = nd->ystar[0] - (out2[0] - nd->EN_star[0]) * nd->k_eps;
+                const double qv1 = nd->ystar[1] - (out2[1] - nd->EN_star[1]) * nd->k_ye;
+                const double y0 = nd->y[0], y1 = nd->y[1];
                 const int mo = k < P.m_outer ? k : P.m_outer;
-                double fh[kMaxOuterMem][2];
-                for (int j = 0; j < kMaxOuterMem; ++j) { fh[j][0] = nd->fh[j][0]; fh[j][1] = nd->fh[j][1]; }
-                double beta[kMaxOuterMem];
-                outer_anderson(fh, mo, beta);
-                double yn0 = 0.0, yn1 = 0.0;
-                for (int j = kMaxOuterMem - mo; j < kMaxOuterMem; ++j) {
-                    yn0 += beta[j] * nd->qh[j][0];
-                    yn1 += beta[j] * nd->qh[j][1];
-                }
-                const int conv = fabs(yn0 - nd->y[0]) <= P.tol_outer * fabs(nd->ystar[0]) &&
-                                 fabs(yn1 - nd->y[1]) <= P.tol_outer * fabs(nd->ystar[1]);   // Algorithm 3
-                nd->y[0] = yn0;
-                nd->y[1] = yn1;
-                int stop = conv;
-                if (!(isfinite(yn0) && isfinite(yn1))) { nd->status |= NMC_NONFINITE; stop = 1; }
-                if (!stop && k >= P.max_outer) { nd->status |= NMC_NOT_CONVERGED_OUTER; stop = 1; }
+                double yn0, yn1;
+                outer_step_warp(nd->qh, nd->fh, qv0, qv1, y0, y1, nd->ri_ys, mo, yn0, yn1);
+                const int conv = fabs(yn0 - y0) <= P.tol_outer * fabs(nd->ystar[0]) &&
+                                 fabs(yn1 - y1) <= P.tol_outer * fabs(nd->ystar[1]);   // Algorithm 3
+                int stop = conv, stb = 0;
+                double Tn = nd->T;
+                if (!(isfinite(yn0) && isfinite(yn1))) { stb |= NMC_NONFINITE; stop = 1; }
+                if (!stop && k >= P.max_outer) { stb |= NMC_NOT_CONVERGED_OUTER; stop = 1; }
                 if (!stop) {
                     bool ok;
-                    const double Tn = eos_temperature(rho, yn0, yn1, nd->T, &ok);
-                    if (ok) nd->T = Tn;
-                    else { nd->status |= NMC_EOS_FAIL; stop = 1; }
+                    const double Tk = eos_temperature(rho, yn0, yn1, Tn, &ok);
+                    if (ok) Tn = Tk;
+                    else { stb |= NMC_EOS_FAIL; stop = 1; }
                 }
-                if (stop) nd->n_outer = k;
-                else append(st.lists + lout * st.C, st.counts + lout, slot);
+                if (tid == 0) {
+                    nd->y[0] = yn0;
+                    nd->y[1] = yn1;
+                    nd->T = Tn;
+                    nd->status |= stb;
+                    if (stop) nd->n_outer = k;
+                    else append(st.lists + lout * st.C, st.counts + lout, slot);
+                }
             }
         }
         __syncthreads();
@@ -455,8 +458,8 @@ __global__ void __launch_bounds__(512) plain_finalize_kernel(const SolveArgs a, 
                 yo0 = nd->y[0]; yo1 = nd->y[1]; To = nd->T;
             } else {
                 if (P.final_q) {   // y = q(M, y) at the converged moments
-                    yo0 = nd->ystar[0] - (out2[0] - nd->EN_star[0]) * kMeVErg / rho;
-                    yo1 = nd->ystar[1] - kMB * (out2[1] - nd->EN_star[1]) / rho;
+                    yo0 = nd->ystar[0] - (out2[0] - nd->EN_star[0]) * nd->k_eps;
+                    yo1 = nd->ystar[1] - (out2[1] - nd->EN_star[1]) * nd->k_ye;
                 } else {
                     yo0 = nd->y[0]; yo1 = nd->y[1];
                 }
