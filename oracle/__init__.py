@@ -20,6 +20,9 @@ equilibrium  Fermi--Dirac projection and the bound-enforcing limiter
 opacities    table interpolation and the NES / pair kernel construction
 solver       rates, the maps Q and q, Anderson acceleration, Algorithm 1,
              and an independent damped-Newton root solve for tiny nodes
+velocity     the O(v/c) solve: Minerbo closure, conserved old moments, the
+             velocity terms of Q and q, the momentum update
+adjoint      the gradient of a converged solve by the implicit-function theorem
 """
 
-from . import constants, grid, eos, equilibrium, opacities, solver  # noqa: F401
+from . import constants, grid, eos, equilibrium, opacities, solver, velocity  # noqa: F401

@@ -187,3 +187,24 @@ def make_inputs(kind, N, energies, ns, seed=0):
         I[..., 0] = D * h
     scale = np.ones((N, 4))
     return dict(rho=rho, T=T, Ye=Ye, D=D, I=I, dt=dt, scale=scale)
+
+
+def make_velocities(kind, N, seed=0, vmax=0.15):
+    """Fluid three-velocities (units of c) for the O(v/c) solve; data only.
+
+    "random": isotropic directions, speeds uniform in [0, vmax].  Otherwise an
+    infall profile along the x axis (the direction of the profile inputs'
+    fluxes), v_x = -2 vmax x / (1 + x^2) with x = r / 100 km (fastest at
+    100 km) over r log-uniform in 10-3000 km, plus transverse components of
+    1% of vmax.
+    """
+    rng = np.random.default_rng(seed + 7919)
+    if kind == "random":
+        d = rng.normal(size=(N, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        return d * rng.uniform(0.0, vmax, size=(N, 1))
+    x = 10.0 ** rng.uniform(1.0, math.log10(3000.0), size=N) / 100.0
+    v = np.zeros((N, 3))
+    v[:, 0] = -2.0 * vmax * x / (1.0 + x * x)
+    v[:, 1:] = 0.01 * vmax * rng.normal(size=(N, 2))
+    return v
