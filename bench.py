@@ -16,7 +16,9 @@ over 2^18 nodes of the same profile and grid, timed the same way; and a
 dt log-uniform 1e-7..1e-5 s), FP64, solved by the persistent fused kernel
 (autotuned once, replayed from a CUDA graph) and by plain per-iteration
 launches (NMC_MODE_PLAIN) on the same inputs; 2^17 nodes by default,
---batching-nodes 4194304 for the full 2^22-node configuration.
+--batching-nodes 4194304 for the full 2^22-node configuration; and a
+"velocity" object: collision_solve_v (the O(v/c) solve with the momentum
+update, FP64) over 2^16 nodes of the profile with an infall velocity field.
 
 Prints one JSON line.  --impl reference times the CPU oracle (the plain FP64
 restatement of the algorithm) on a bounded sample of the same workload.
@@ -45,7 +47,8 @@ WORKLOAD = ("collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, EmAb
 # DRAM bytes (read + write) per node of one launch, from ncu captures of the 2^16-node profile
 # (dram__bytes_read.sum + dram__bytes_write.sum); traffic grows with the node count.  None where
 # the kernel has changed since its counters were taken.
-TRAFFIC_PER_NODE = {"fused_kernel<double>": None, "fused_kernel<float>": None, "adjoint_kernel": None}
+TRAFFIC_PER_NODE = {"fused_kernel<double>": 521435392 / 65536, "fused_kernel<float>": None,
+                    "adjoint_kernel": 875135232 / 65536, "velocity_kernel": None}
 
 
 def _traffic(kernel, n):
@@ -55,6 +58,8 @@ FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64: 152 SMs x 4 flop/clk x 2.07 GHz 
 CPU_SAMPLE = 48           # oracle sample (nodes) for the CPU baseline
 ADJ_NODES = 1 << 18
 BATCH_NODES = 1 << 17
+VEL_WORKLOAD = ("O(v/c) solve (collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, all processes, "
+                "infall velocity field up to 0.15 c, Minerbo closure, FP64, tol 1e-10, Anderson depth 3)")
 ADJ_WORKLOAD = ("gradient of the FP64 solve (collapse profile, 2^18 nodes, 4 species, Grid C 16x2 energies, "
                 "all processes, forward tol 1e-10) w.r.t. J, H, Ye, T and the 4 opacity scales, "
                 "cotangents on J, H, Ye, eps, T")
@@ -70,6 +75,8 @@ def _args():
     ap.add_argument("--adjoint-nodes", type=int, default=ADJ_NODES, help="0 skips the adjoint measurement")
     ap.add_argument("--batching-nodes", type=int, default=BATCH_NODES,
                     help="nodes of the persistent-vs-plain comparison (0 skips it)")
+    ap.add_argument("--velocity-nodes", type=int, default=N_NODES,
+                    help="nodes of the O(v/c) solve measurement (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="path reported as the headline value (both are timed)")
@@ -220,6 +227,50 @@ def _time_path(ctx, prm, t, out, steps, warmup, barrier, stream):
     per_step = [a.elapsed_time(b) for a, b in evs]
     total_ms = evs[0][0].elapsed_time(evs[-1][1])
     return per_step, total_ms
+
+
+def time_velocity(args, ctx, eps, dev, rank, barrier, allmax, stream):
+    """Time collision_solve_v (the O(v/c) solve, FP64) over the profile with an infall velocity field."""
+    import torch
+    from paper_2601_00976_gb300 import nmc, synthetic, flops
+    from paper_2601_00976_gb300.dist import workload_seed, weak_scaling_value
+    n = args.velocity_nodes
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    inp = synthetic.make_inputs("profile", n, eps, NS, seed=workload_seed(rank, 3))
+    t = {k: torch.tensor(v, device=dev) for k, v in inp.items()}
+    v = torch.tensor(synthetic.make_velocities("profile", n, seed=workload_seed(rank, 3)), device=dev)
+    p = nmc.default_params(tol_inner=TOL, tol_outer=TOL, m_inner=MEM, m_outer=MEM)
+    out = ctx.collision_solve_v(p, t["rho"], t["T"], t["Ye"], v, t["D"], t["I"], t["dt"], t["scale"])
+
+    def step():
+        ctx.collision_solve_v(p, t["rho"], t["T"], t["Ye"], v, t["D"], t["I"], t["dt"], t["scale"], out=out)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    barrier()
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    total_ms = allmax(evs[0][0].elapsed_time(evs[-1][1]))
+    n_in = out["n_inner"].cpu().numpy().astype(np.int64)
+    n_out = out["n_outer"].cpu().numpy().astype(np.int64)
+    fl = float(np.sum(flops.velocity_node_flops(NS, len(eps), N_ELEM, NQ, MEM, n_in, n_out)))
+    ach = fl / (kern_ms * 1e-3) / 1e12
+    vmag = torch.sqrt((v * v).sum(1))
+    return {"metric": "converged O(v/c) collision solves/s (nodes*steps/s)",
+            "value": weak_scaling_value(ws * n, args.steps, total_ms), "unit": "solves/s",
+            "ms_per_step": total_ms / args.steps, "dtype": "f64",
+            "config": {"workload": VEL_WORKLOAD, "nodes_per_gpu": n, "max_speed_c": float(vmag.max().item()),
+                       "converged_fraction": float((out["status"] == 0).float().mean().item()),
+                       "mean_inner_iters": float(n_in.mean()), "mean_outer_iters": float(n_out.mean())},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS, "traffic": _traffic("velocity_kernel", n),
+                         "kernel": "velocity_kernel", "peak_source": "derived FP64 FMA rate at 2.07 GHz",
+                         "algorithmic_flops_per_launch": fl, "kernel_ms": kern_ms}}
 
 
 def time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream):
@@ -391,6 +442,7 @@ def run_nmc(args):
     barrier()
     e2e_s = allmax((time.perf_counter() - t0) / e2e_steps)
 
+    vel = time_velocity(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.velocity_nodes > 0 else None
     adj = time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.adjoint_nodes > 0 else None
     bat = time_batching(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.batching_nodes > 0 else None
 
@@ -436,6 +488,8 @@ def run_nmc(args):
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
         }
+        if vel is not None:
+            line["velocity"] = vel
         if adj is not None:
             line["adjoint"] = adj
         if bat is not None:

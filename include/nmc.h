@@ -202,6 +202,38 @@ int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n,
                     void* stream);
 
 /*
+ * SolveNeutrinoMatterCoupling (Algorithm 1) with the O(v/c) terms of Sec. 3.5
+ * at n independent nodes, FP64: the moment map of Eq. implicitMomentsNodal
+ * with v^i I_i, v^i K_ij (Minerbo closure, Eqs. eddingtonTensor and
+ * eddingtonFactorMinerbo) and lambda = 1/(1+|v|); the old state's conserved
+ * moments N* = D* + v*.I*, G*_j = I*_j + v*^i K_ij(M*) (Eq.
+ * conservedToPrimitive); the matter map of Eq. implicitFluidNodal with the
+ * momentum update and Eqs. eulerianMomentumLG, eulerianEnergyLG,
+ * eulerianNumberLG.  Flat metric at the node (Cartesian components).
+ *
+ * Arguments as collision_solve, plus:
+ *   v_in[n][3]  (DEVICE)  fluid three-velocity v* in units of c, |v*| < 1
+ *   freeze_velocity       1: v stays v* (the momentum update is switched off,
+ *                         as in the deleptonization setup of Sec. 6)
+ *   v_floor > 0           reference speed of Algorithm 3 for the velocity
+ *                         components: |delta v_j| <= tol * max(|v*|, v_floor)
+ *   v_out[n][3] (DEVICE)  the new velocity
+ * eps_out is the specific internal energy eps = eps_f - v^2 c^2 / 2.  With
+ * final_q the returned (v, eps_f, Ye) conserve momentum, total energy and
+ * lepton number to rounding (v solves the momentum update exactly).
+ * Supported: NMC_FP64, NMC_MODE_FUSED, m_inner <= 3 and m_outer <= 3
+ * (NMC_EUNSUPPORTED otherwise).  An invalid node (also |v*| >= 1 or a
+ * non-finite v*) returns its inputs with NMC_BAD_INPUT.
+ */
+int collision_solve_v(nmc_ctx* ctx, const nmc_params* params, int64_t n,
+                      const double* rho, const double* T_in, const double* Ye_in, const double* v_in,
+                      const double* J_in, const double* H_in, const double* dt,
+                      const double* opac_scale, int32_t freeze_velocity, double v_floor,
+                      double* J_out, double* H_out, double* v_out, double* Ye_out, double* eps_out,
+                      double* T_out, int32_t* n_outer, int32_t* n_inner, uint32_t* status,
+                      void* stream);
+
+/*
  * collision_solve without device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory when
  * they solve, for example a simulation framework that reserves the GPU's

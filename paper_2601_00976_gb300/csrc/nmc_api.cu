@@ -392,6 +392,35 @@ int collision_solve(nmc_ctx* ctx, const nmc_params* params, int64_t n, const dou
     return launch_fused(ctx, a, static_cast<cudaStream_t>(stream));
 }
 
+int collision_solve_v(nmc_ctx* ctx, const nmc_params* params, int64_t n, const double* rho,
+                      const double* T_in, const double* Ye_in, const double* v_in, const double* J_in,
+                      const double* H_in, const double* dt, const double* opac_scale, int32_t freeze_velocity,
+                      double v_floor, double* J_out, double* H_out, double* v_out, double* Ye_out,
+                      double* eps_out, double* T_out, int32_t* n_outer, int32_t* n_inner, uint32_t* status,
+                      void* stream) {
+    if (!ctx) return NMC_EINVAL;
+    int rc = nmc_check_params_internal(ctx, params);
+    if (rc != NMC_OK) return rc;
+    if (n < 0) return set_error(ctx, NMC_EINVAL, "n < 0");
+    if (n > (int64_t(1) << 30)) return set_error(ctx, NMC_EUNSUPPORTED, "n > 2^30 nodes per call");
+    if (!(v_floor > 0.0) || !std::isfinite(v_floor)) return set_error(ctx, NMC_EINVAL, "v_floor must be > 0");
+    if (params->mode != NMC_MODE_FUSED) return set_error(ctx, NMC_EUNSUPPORTED, "the O(v/c) solve runs fused");
+    if (n == 0) return NMC_OK;
+    if (!rho || !T_in || !Ye_in || !v_in || !J_in || !H_in || !dt || !J_out || !H_out || !v_out || !Ye_out ||
+        !eps_out || !T_out || !n_outer || !n_inner || !status)
+        return set_error(ctx, NMC_EINVAL, "null array argument");
+    SolveArgs a{};
+    a.g = ctx->g;
+    a.tb = ctx->tb;
+    a.p = *params;
+    a.n = n;
+    a.rho = rho; a.T = T_in; a.Ye = Ye_in; a.J = J_in; a.H = H_in; a.dt = dt; a.scale = opac_scale;
+    a.J_out = J_out; a.H_out = H_out; a.Ye_out = Ye_out; a.eps_out = eps_out; a.T_out = T_out;
+    a.n_outer = n_outer; a.n_inner = n_inner; a.status = status;
+    a.queue = ctx->queue;
+    return launch_velocity(ctx, a, v_in, v_out, freeze_velocity ? 1 : 0, v_floor, static_cast<cudaStream_t>(stream));
+}
+
 int nmc_autotune(nmc_ctx* ctx, const nmc_params* params, int64_t n, const double* rho, const double* T_in,
                  const double* Ye_in, const double* J_in, const double* H_in, const double* dt,
                  const double* opac_scale, double* J_out, double* H_out, double* Ye_out, double* eps_out,

@@ -170,6 +170,8 @@ int launch_opacity_interp(nmc_ctx* ctx, int which, int species, long long p, con
 size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, bool mixed, SolveArgs* a);
 int launch_adjoint(nmc_ctx* ctx, AdjointArgs& a, cudaStream_t stream);
 int launch_plain(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream);
+int launch_velocity(nmc_ctx* ctx, const SolveArgs& a, const double* v_in, double* v_out, int freeze,
+                    double v_floor, cudaStream_t stream);
 int launch_fused_f64_m3(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
 int launch_fused_f64_m5(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
 int launch_fused_f32_m3(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);

@@ -62,3 +62,18 @@ def adjoint_flops(ns, ne, n_elem, nq, with_h=True):
     f += 18 * ns * ne * ne + (8 * ns * ne * ne if with_h else 0)
     f += (ns // 2) * (2 * n2 ** 3 // 3 + 6 * n2 * n2)
     return f + 30 * ns * ne
+
+
+def velocity_node_flops(ns, ne, n_elem, nq, m, n_inner, n_outer):
+    """Flops of one node of the O(v/c) solve: node_flops plus the velocity terms.
+
+    per inner iteration and bin: the closure (|I|, h, Minerbo psi, the two
+    coefficients of K: ~25), v.I and v^i K_ij (~11), the lambda-form map of
+    D and I (~14)                                              -> 50 ns ne
+    per outer iteration: the fifteen Eulerian terms per bin (~25) and the
+    five-component matter update and least squares (~100)      -> 25 ns ne + 100
+    once: the old state's conserved moments and Eulerian sums (~65 per bin)
+    and the final momentum solve with its sums (~100)          -> 65 ns ne + 100
+    """
+    return (node_flops(ns, ne, n_elem, nq, m, n_inner, n_outer) + n_inner * 50 * ns * ne
+            + n_outer * (25 * ns * ne + 100) + 65 * ns * ne + 100)

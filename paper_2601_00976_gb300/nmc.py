@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
 
 
 EXPORTS = ("nmc_default_params", "nmc_create", "nmc_destroy", "nmc_last_error", "nmc_energy_nodes",
-           "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "collision_solve_noalloc",
+           "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "collision_solve_noalloc", "collision_solve_v",
            "opacity_interp", "collision_adjoint", "nmc_set_plain_chunk", "nmc_autotune")
 
 _lib = None
@@ -89,6 +89,9 @@ def load_library(path=LIB_PATH):
     lib.collision_solve.restype = ctypes.c_int
     lib.collision_solve_noalloc.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 16
     lib.collision_solve_noalloc.restype = ctypes.c_int
+    lib.collision_solve_v.argtypes = ([vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 8 +
+                                      [ctypes.c_int32, ctypes.c_double] + [vp] * 10)
+    lib.collision_solve_v.restype = ctypes.c_int
     lib.opacity_interp.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64] + [vp] * 6
     lib.opacity_interp.restype = ctypes.c_int
     lib.collision_adjoint.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 20
@@ -239,6 +242,36 @@ class Context:
         self._check(rc, "collision_solve")
         if host:
             out = {k: v.to("cpu", non_blocking=False) for k, v in out.items()}
+        return out
+
+    def collision_solve_v(self, params, rho, T, Ye, v, J, H, dt, scale=None, freeze_velocity=False,
+                          v_floor=1e-6, out=None, stream=None):
+        """Run collision_solve_v (the O(v/c) solve) on CUDA float64 tensors; v has shape (n, 3)
+        in units of c.  Returns the outputs of collision_solve plus "v" (n, 3); "eps" is the
+        specific internal energy."""
+        import torch
+        ins = [rho, T, Ye, v, J, H, dt] + ([scale] if scale is not None else [])
+        for x in ins:
+            if x.dtype != torch.float64 or not x.is_contiguous() or not x.is_cuda:
+                raise ValueError("inputs must be contiguous CUDA float64 tensors")
+        n = rho.shape[0]
+        ns, ne = self.n_species, self.ne
+        if J.shape != (n, ns, ne) or H.shape != (n, ns, ne, 3) or v.shape != (n, 3):
+            raise ValueError(f"J must be {(n, ns, ne)}, H {(n, ns, ne, 3)} and v {(n, 3)}")
+        if out is None:
+            f64 = dict(dtype=torch.float64, device=rho.device)
+            out = dict(J=torch.empty_like(J), H=torch.empty_like(H), v=torch.empty_like(v),
+                       Ye=torch.empty(n, **f64), eps=torch.empty(n, **f64), T=torch.empty(n, **f64),
+                       n_outer=torch.empty(n, dtype=torch.int32, device=rho.device),
+                       n_inner=torch.empty(n, dtype=torch.int32, device=rho.device),
+                       status=torch.empty(n, dtype=torch.int32, device=rho.device))
+        p = lambda x: ctypes.c_void_p(x.data_ptr()) if x is not None else None  # noqa: E731
+        rc = self._lib.collision_solve_v(
+            self._h, ctypes.byref(params), n, p(rho), p(T), p(Ye), p(v), p(J), p(H), p(dt), p(scale),
+            1 if freeze_velocity else 0, float(v_floor),
+            p(out["J"]), p(out["H"]), p(out["v"]), p(out["Ye"]), p(out["eps"]), p(out["T"]),
+            p(out["n_outer"]), p(out["n_inner"]), p(out["status"]), self._stream_handle(stream))
+        self._check(rc, "collision_solve_v")
         return out
 
     def collision_adjoint(self, params, rho, T, Ye, J, H, dt, scale, J_out, T_out=None,

@@ -11,7 +11,7 @@ import multiprocessing as mp
 
 import numpy as np
 
-from oracle import grid as ogrid, solver as osolver, adjoint as oadjoint
+from oracle import grid as ogrid, solver as osolver, adjoint as oadjoint, velocity as ovel
 from paper_2601_00976_gb300 import synthetic
 
 _TABLES = {}
@@ -51,6 +51,15 @@ def node_condition(task):
     r = osolver.solve_node(g, tables, params, x["rho"], x["T"], x["Ye"], x["D"], x["I"], x["dt"], x["scale"])
     return oadjoint.condition_number(g, tables, params, x["rho"], x["T"], x["Ye"], x["D"], x["I"], x["dt"],
                                      x["scale"], r["D"])
+
+
+def node_velocity(task):
+    """Oracle O(v/c) solve of one node; task as node_gradient's plus "v" and "freeze" in x."""
+    g, tables = _grid_tables(*task["case"])
+    x = task["x"]
+    params = osolver.Params(**task["params"])
+    return ovel.solve_node(g, tables, params, x["rho"], x["T"], x["Ye"], x["v"], x["D"], x["I"], x["dt"],
+                           x["scale"], freeze_velocity=x.get("freeze", False))
 
 
 def run(tasks, fn=node_gradient, workers=None):
