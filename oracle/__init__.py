@@ -22,7 +22,9 @@ solver       rates, the maps Q and q, Anderson acceleration, Algorithm 1,
              and an independent damped-Newton root solve for tiny nodes
 velocity     the O(v/c) solve: Minerbo closure, conserved old moments, the
              velocity terms of Q and q, the momentum update
+c2p          conserved-to-primitive moment recovery (Anderson-accelerated
+             fixed point of Sec. 3.4)
 adjoint      the gradient of a converged solve by the implicit-function theorem
 """
 
-from . import constants, grid, eos, equilibrium, opacities, solver, velocity  # noqa: F401
+from . import constants, grid, eos, equilibrium, opacities, solver, velocity, c2p  # noqa: F401
