@@ -18,7 +18,8 @@ dt log-uniform 1e-7..1e-5 s), FP64, solved by the persistent fused kernel
 launches (NMC_MODE_PLAIN) on the same inputs; 2^17 nodes by default,
 --batching-nodes 4194304 for the full 2^22-node configuration; and a
 "velocity" object: collision_solve_v (the O(v/c) solve with the momentum
-update, FP64) over 2^16 nodes of the profile with an infall velocity field.
+update, FP64) over 2^16 nodes of the profile with an infall velocity field;
+and a "c2p" object: conserved_to_primitive over every bin of 2^16 nodes.
 
 Prints one JSON line.  --impl reference times the CPU oracle (the plain FP64
 restatement of the algorithm) on a bounded sample of the same workload.
@@ -48,7 +49,7 @@ WORKLOAD = ("collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, EmAb
 # (dram__bytes_read.sum + dram__bytes_write.sum); traffic grows with the node count.  None where
 # the kernel has changed since its counters were taken.
 TRAFFIC_PER_NODE = {"fused_kernel<double>": 521435392 / 65536, "fused_kernel<float>": None,
-                    "adjoint_kernel": 875135232 / 65536, "velocity_kernel": None}
+                    "adjoint_kernel": 875135232 / 65536, "velocity_kernel": None, "c2p_kernel": None}
 
 
 def _traffic(kernel, n):
@@ -58,6 +59,10 @@ FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64: 152 SMs x 4 flop/clk x 2.07 GHz 
 CPU_SAMPLE = 48           # oracle sample (nodes) for the CPU baseline
 ADJ_NODES = 1 << 18
 BATCH_NODES = 1 << 17
+C2P_WORKLOAD = ("conserved-to-primitive recovery of every bin (collapse profile, 2^16 nodes x 4 species x 32 "
+                "energies, conserved moments of the profile's occupations, infall velocity up to 0.15 c), FP64, "
+                "tol 1e-8, Anderson memory 3")
+C2P_BYTES_PER_BIN = 68    # N, G in; D, I, iteration count out (8 + 24 + 8 + 24 + 4 bytes)
 VEL_WORKLOAD = ("O(v/c) solve (collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, all processes, "
                 "infall velocity field up to 0.15 c, Minerbo closure, FP64, tol 1e-10, Anderson depth 3)")
 ADJ_WORKLOAD = ("gradient of the FP64 solve (collapse profile, 2^18 nodes, 4 species, Grid C 16x2 energies, "
@@ -77,6 +82,8 @@ def _args():
                     help="nodes of the persistent-vs-plain comparison (0 skips it)")
     ap.add_argument("--velocity-nodes", type=int, default=N_NODES,
                     help="nodes of the O(v/c) solve measurement (0 skips it)")
+    ap.add_argument("--c2p-nodes", type=int, default=N_NODES,
+                    help="nodes of the conserved-to-primitive measurement (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="path reported as the headline value (both are timed)")
@@ -273,6 +280,52 @@ def time_velocity(args, ctx, eps, dev, rank, barrier, allmax, stream):
                          "algorithmic_flops_per_launch": fl, "kernel_ms": kern_ms}}
 
 
+def time_c2p(args, ctx, eps, dev, rank, barrier, allmax, stream):
+    """Time conserved_to_primitive (FP64) on every bin of the profile with an infall velocity field."""
+    import torch
+    from paper_2601_00976_gb300 import synthetic, flops
+    from paper_2601_00976_gb300.dist import workload_seed, weak_scaling_value
+    n = args.c2p_nodes
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    inp = synthetic.make_inputs("profile", n, eps, NS, seed=workload_seed(rank, 4))
+    # conserved moments of the same shape and realizability as the profile's primitive ones
+    N = torch.tensor(inp["D"], device=dev)
+    G = torch.tensor(inp["I"], device=dev)
+    v = torch.tensor(synthetic.make_velocities("profile", n, seed=workload_seed(rank, 4)), device=dev)
+    out = ctx.conserved_to_primitive(N, G, v)
+
+    def step():
+        ctx.conserved_to_primitive(N, G, v, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    barrier()
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    total_ms = allmax(evs[0][0].elapsed_time(evs[-1][1]))
+    it = out["iters"].cpu().numpy().astype(np.int64)
+    bins = it.size
+    fl = float(np.sum(flops.c2p_bin_flops(it)))
+    ach = fl / (kern_ms * 1e-3) / 1e12
+    byts = bins * C2P_BYTES_PER_BIN + n * 24
+    return {"metric": "conserved-to-primitive recoveries/s (bins*steps/s)",
+            "value": weak_scaling_value(ws * bins, args.steps, total_ms), "unit": "bins/s",
+            "ms_per_step": total_ms / args.steps, "dtype": "f64",
+            "config": {"workload": C2P_WORKLOAD, "nodes_per_gpu": n, "bins_per_gpu": bins,
+                       "mean_iters": float(it.mean()), "max_iters": int(it.max()),
+                       "converged_fraction": float((out["status"] == 0).float().mean().item()),
+                       "hbm_gbs_algorithmic": byts / (kern_ms * 1e-3) / 1e9},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS, "traffic": _traffic("c2p_kernel", n),
+                         "kernel": "c2p_kernel", "peak_source": "derived FP64 FMA rate at 2.07 GHz",
+                         "algorithmic_flops_per_launch": fl, "kernel_ms": kern_ms}}
+
+
 def time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream):
     """Time collision_adjoint over the adjoint workload (inputs and cotangents resident in HBM)."""
     import torch
@@ -443,6 +496,7 @@ def run_nmc(args):
     e2e_s = allmax((time.perf_counter() - t0) / e2e_steps)
 
     vel = time_velocity(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.velocity_nodes > 0 else None
+    c2p = time_c2p(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.c2p_nodes > 0 else None
     adj = time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.adjoint_nodes > 0 else None
     bat = time_batching(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.batching_nodes > 0 else None
 
@@ -490,6 +544,8 @@ def run_nmc(args):
         }
         if vel is not None:
             line["velocity"] = vel
+        if c2p is not None:
+            line["c2p"] = c2p
         if adj is not None:
             line["adjoint"] = adj
         if bat is not None:

@@ -234,6 +234,27 @@ int collision_solve_v(nmc_ctx* ctx, const nmc_params* params, int64_t n,
                       void* stream);
 
 /*
+ * Conserved-to-primitive moment recovery (Sec. 3.4, Eqs. conservedToPrimitive,
+ * c2p_FP, c2p_sequence), FP64, at n nodes of the context's shape.  For every
+ * (node, species, energy) bin it finds M = (D, I_j) with N = D + v^i I_i and
+ * G_j = I_j + v^i K_ij(M) (Minerbo closure, flat metric), iterating
+ * M <- (1 - lam) M + lam (N - v.I, G - v.K(M)), lam = 1/(1 + |v|), from M = U
+ * with Anderson acceleration of the given memory until
+ * ||M_new - M|| <= tol ||U|| (Euclidean norms of the bin's 4-vector).
+ *
+ * Inputs (DEVICE, float64): N_in[n][ns][ne], G_in[n][ns][ne][3], v[n][3]
+ * (units of c).  Outputs (DEVICE): D_out, I_out (same shapes), iters[n][ns][ne]
+ * (iterations per bin; may be NULL), status[n]: NMC_NOT_CONVERGED_INNER if
+ * some bin reached max_iter, NMC_NONFINITE if some bin went non-finite.
+ * tol > 0, memory in 1..3, max_iter >= 1 (NMC_EINVAL otherwise);
+ * ns * ne <= 256 (NMC_EUNSUPPORTED otherwise).  The paper's default tol is 1e-8.
+ */
+int conserved_to_primitive(nmc_ctx* ctx, int64_t n, const double* N_in, const double* G_in,
+                           const double* v, double tol, int32_t memory, int32_t max_iter,
+                           double* D_out, double* I_out, int32_t* iters, uint32_t* status,
+                           void* stream);
+
+/*
  * collision_solve without device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory when
  * they solve, for example a simulation framework that reserves the GPU's

@@ -421,6 +421,21 @@ int collision_solve_v(nmc_ctx* ctx, const nmc_params* params, int64_t n, const d
     return launch_velocity(ctx, a, v_in, v_out, freeze_velocity ? 1 : 0, v_floor, static_cast<cudaStream_t>(stream));
 }
 
+int conserved_to_primitive(nmc_ctx* ctx, int64_t n, const double* N_in, const double* G_in, const double* v,
+                           double tol, int32_t memory, int32_t max_iter, double* D_out, double* I_out,
+                           int32_t* iters, uint32_t* status, void* stream) {
+    if (!ctx) return NMC_EINVAL;
+    if (n < 0) return set_error(ctx, NMC_EINVAL, "n < 0");
+    if (n > (int64_t(1) << 30)) return set_error(ctx, NMC_EUNSUPPORTED, "n > 2^30 nodes per call");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(ctx, NMC_EINVAL, "tol must be > 0");
+    if (memory < 1 || memory > 3) return set_error(ctx, NMC_EINVAL, "memory must be 1..3");
+    if (max_iter < 1) return set_error(ctx, NMC_EINVAL, "max_iter must be >= 1");
+    if (n == 0) return NMC_OK;
+    if (!N_in || !G_in || !v || !D_out || !I_out || !status) return set_error(ctx, NMC_EINVAL, "null array argument");
+    return launch_c2p(ctx, n, N_in, G_in, v, tol, memory, max_iter, D_out, I_out, iters, status,
+                      static_cast<cudaStream_t>(stream));
+}
+
 int nmc_autotune(nmc_ctx* ctx, const nmc_params* params, int64_t n, const double* rho, const double* T_in,
                  const double* Ye_in, const double* J_in, const double* H_in, const double* dt,
                  const double* opac_scale, double* J_out, double* H_out, double* Ye_out, double* eps_out,

@@ -281,8 +281,10 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                             // rounding is relative to the net rate, not to the gross rates that are
                             // dtau chi ~ 1e4 times larger in optically thick matter.  Each product is
                             // formed with the same operands in the two bins it couples and
-                            // fl(e1 - e2) in bin q is exactly minus its counterpart in bin j, so NES
-                            // conserves number to the rounding of the sums.
+                            // fl(e1 - e2) in bin q is exactly minus its counterpart in bin j, so the
+                            // map conserves number to the rounding of the sums: NES then leaves no
+                            // rounding source in the slowly damped number-conserving mode (factored
+                            // into dot products, it raised the heavy flavours' error 20-fold).
                             const R* w = vWdev + s * NEP;
                             const R wq = w[q], vq = y[q];
                             for (int j = 0; j < NE; ++j) {
@@ -308,24 +310,21 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         // mixed: the pair (q, j) is produced at K_Ann p_q pbar_j and annihilated at
                         // K_Ann u_q ubar_j (p = a v); with u = w + p the net gain of either bin is
                         // -K_Ann (w_P w_A + w_P p_A + p_P w_A) (P particle, A antiparticle),
-                        // proportional to the deviations and formed from the same operands, in
-                        // the same order, in the particle's and the antiparticle's sums
+                        // proportional to the deviations.  Summed over j, with s the bin's own
+                        // species and t its partner, it is -(w_s (C + X) + p_s C) with
+                        // C = sum_j K w_t,j and X = sum_j K p_t,j (the emissivity's dot product).
                         const bool part = (s & 1) == 0;
-                        const R ws = kMixed ? vWdev[sq] : (R)0, ps = kMixed ? vAW1D[sq] : (R)0;
                         const R* wpt = vWdev + pt * NEP;
                         const int stride_j = part ? 1 : LD;
                         const int base = part ? q * LD : q;
+                        R cw = 0;
                         for (int j = 0; j < NE; ++j) {
                             const R av = A0[base + j * stride_j];
                             pro = r_fma(av, x[j], pro);
                             an = r_fma(av, y[j], an);
-                            if constexpr (kMixed) {
-                                const R wP = part ? ws : wpt[j], pP = part ? ps : x[j];
-                                const R wA = part ? wpt[j] : ws, pA = part ? x[j] : ps;
-                                const R tt = __fadd_rn(__fadd_rn(__fmul_rn(wP, wA), __fmul_rn(wP, pA)), __fmul_rn(pP, wA));
-                                cp = __fsub_rn(cp, __fmul_rn(av, tt));
-                            }
+                            if constexpr (kMixed) cw = r_fma(av, wpt[j], cw);
                         }
+                        if constexpr (kMixed) cp = -r_fma(vWdev[sq], cw + pro, vAW1D[sq] * cw);
                         pro *= vA[sq];
                     }
                     const R eta = chiab * deq + nin + pro;          // dtau * Eq. emissivityNodal

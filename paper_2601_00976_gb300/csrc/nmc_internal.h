@@ -172,6 +172,9 @@ int launch_adjoint(nmc_ctx* ctx, AdjointArgs& a, cudaStream_t stream);
 int launch_plain(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream);
 int launch_velocity(nmc_ctx* ctx, const SolveArgs& a, const double* v_in, double* v_out, int freeze,
                     double v_floor, cudaStream_t stream);
+int launch_c2p(nmc_ctx* ctx, long long n, const double* N, const double* G, const double* v, double tol,
+               int memory, int max_iter, double* D, double* I, int32_t* iters, uint32_t* status,
+               cudaStream_t stream);
 int launch_fused_f64_m3(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
 int launch_fused_f64_m5(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
 int launch_fused_f32_m3(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);

@@ -77,3 +77,15 @@ def velocity_node_flops(ns, ne, n_elem, nq, m, n_inner, n_outer):
     """
     return (node_flops(ns, ne, n_elem, nq, m, n_inner, n_outer) + n_inner * 50 * ns * ne
             + n_outer * (25 * ns * ne + 100) + 65 * ns * ne + 100)
+
+
+def c2p_bin_flops(iters):
+    """Flops of one bin's conserved-to-primitive recovery with `iters` iterations.
+
+    per iteration: the closure (|I|, h, Minerbo psi, K's two coefficients: ~25),
+    v.I and the map of D and I (~20), the residual and the four-vector dot
+    products of the eliminated normal equations (~40), the 2 x 2 solve (~15),
+    the mixing and the stopping norm (~20)                        -> 120
+    once: lambda and the reference norm                              -> 10
+    """
+    return 120 * iters + 10

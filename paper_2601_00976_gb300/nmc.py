@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
 
 
 EXPORTS = ("nmc_default_params", "nmc_create", "nmc_destroy", "nmc_last_error", "nmc_energy_nodes",
-           "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "collision_solve_noalloc", "collision_solve_v",
+           "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "collision_solve_noalloc", "collision_solve_v", "conserved_to_primitive",
            "opacity_interp", "collision_adjoint", "nmc_set_plain_chunk", "nmc_autotune")
 
 _lib = None
@@ -92,6 +92,9 @@ def load_library(path=LIB_PATH):
     lib.collision_solve_v.argtypes = ([vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 8 +
                                       [ctypes.c_int32, ctypes.c_double] + [vp] * 10)
     lib.collision_solve_v.restype = ctypes.c_int
+    lib.conserved_to_primitive.argtypes = ([vp, ctypes.c_int64, vp, vp, vp, ctypes.c_double, ctypes.c_int32,
+                                            ctypes.c_int32] + [vp] * 5)
+    lib.conserved_to_primitive.restype = ctypes.c_int
     lib.opacity_interp.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64] + [vp] * 6
     lib.opacity_interp.restype = ctypes.c_int
     lib.collision_adjoint.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 20
@@ -272,6 +275,28 @@ class Context:
             p(out["J"]), p(out["H"]), p(out["v"]), p(out["Ye"]), p(out["eps"]), p(out["T"]),
             p(out["n_outer"]), p(out["n_inner"]), p(out["status"]), self._stream_handle(stream))
         self._check(rc, "collision_solve_v")
+        return out
+
+    def conserved_to_primitive(self, N, G, v, tol=1e-8, memory=3, max_iter=100, out=None, stream=None):
+        """Run conserved_to_primitive on CUDA float64 tensors N (n, ns, ne), G (n, ns, ne, 3),
+        v (n, 3); returns D, I, iters (per bin) and status (per node)."""
+        import torch
+        for x in (N, G, v):
+            if x.dtype != torch.float64 or not x.is_contiguous() or not x.is_cuda:
+                raise ValueError("inputs must be contiguous CUDA float64 tensors")
+        n = N.shape[0]
+        ns, ne = self.n_species, self.ne
+        if N.shape != (n, ns, ne) or G.shape != (n, ns, ne, 3) or v.shape != (n, 3):
+            raise ValueError(f"N must be {(n, ns, ne)}, G {(n, ns, ne, 3)} and v {(n, 3)}")
+        if out is None:
+            out = dict(D=torch.empty_like(N), I=torch.empty_like(G),
+                       iters=torch.empty((n, ns, ne), dtype=torch.int32, device=N.device),
+                       status=torch.empty(n, dtype=torch.int32, device=N.device))
+        p = lambda x: ctypes.c_void_p(x.data_ptr()) if x is not None else None  # noqa: E731
+        rc = self._lib.conserved_to_primitive(self._h, n, p(N), p(G), p(v), float(tol), int(memory), int(max_iter),
+                                              p(out["D"]), p(out["I"]), p(out["iters"]), p(out["status"]),
+                                              self._stream_handle(stream))
+        self._check(rc, "conserved_to_primitive")
         return out
 
     def collision_adjoint(self, params, rho, T, Ye, J, H, dt, scale, J_out, T_out=None,
