@@ -40,16 +40,20 @@ struct C2pArgs {
     uint32_t* status;     // [n]
 };
 
-// g(M) of Eq. c2p_FP for one bin.
+// g(M) of Eq. c2p_FP for one bin.  The flux factor h = |I| / D and the coefficient c ~ D / |I|^2
+// come from one reciprocal of D and one reciprocal square root of |I|^2: FP64 division and square
+// root are instruction sequences on the FP64 pipe, which bounds this kernel.
 __device__ __forceinline__ void c2p_map(const double (&M)[4], double N, const double* G, const double* v,
                                         double lam, double (&g)[4]) {
     const double In2 = M[1] * M[1] + M[2] * M[2] + M[3] * M[3];
-    const double In = sqrt(In2);
-    double h = M[0] > 0.0 ? In / M[0] : 0.0;
+    const bool hasI = In2 > 0.0, hasD = M[0] > 0.0;
+    const double rIn = hasI ? rsqrt(In2) : 0.0;   // 1 / |I|
+    const double rD = hasD ? 1.0 / M[0] : 0.0;
+    double h = In2 * rIn * rD;
     h = fmin(fmax(h, 0.0), 1.0);
     const double psi = 1.0 / 3.0 + (2.0 / 15.0) * (3.0 - h + 3.0 * h * h) * h * h;
     const double a = 0.5 * (1.0 - psi) * M[0];
-    const double c = In2 > 0.0 ? 0.5 * (3.0 * psi - 1.0) * M[0] / In2 : 0.0;
+    const double c = 0.5 * (3.0 * psi - 1.0) * M[0] * rIn * rIn;
     const double vI = v[0] * M[1] + v[1] * M[2] + v[2] * M[3];
     const double ml = 1.0 - lam;
     g[0] = ml * M[0] + lam * (N - vI);
@@ -71,7 +75,8 @@ __global__ void __launch_bounds__(256) c2p_kernel(const C2pArgs a) {
             const double Nv = a.N[o];
             const double G[3] = {a.G[o * 3 + 0], a.G[o * 3 + 1], a.G[o * 3 + 2]};
             double M[4] = {Nv, G[0], G[1], G[2]};
-            const double ref = a.tol * sqrt(Nv * Nv + G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+            // the stopping test ||M_new - M|| <= tol ||U||, squared
+            const double ref2 = a.tol * a.tol * (Nv * Nv + G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
             double Fh[3][4], Gh[3][4];   // residual and map-value history, newest last
             for (int j = 0; j < 3; ++j)
                 for (int c = 0; c < 4; ++c) { Fh[j][c] = 0.0; Gh[j][c] = 0.0; }
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(256) c2p_kernel(const C2pArgs a) {
                 double d2 = 0.0;
                 for (int c = 0; c < 4; ++c) { const double d = Mn[c] - M[c]; d2 += d * d; M[c] = Mn[c]; }
                 if (!(isfinite(M[0]) && isfinite(M[1]) && isfinite(M[2]) && isfinite(M[3]))) break;
-                if (sqrt(d2) <= ref) { conv = 1; break; }
+                if (d2 <= ref2) { conv = 1; break; }
             }
             fail = conv ? 0 : (isfinite(M[0]) && isfinite(M[1]) && isfinite(M[2]) && isfinite(M[3])
                                    ? (int)NMC_NOT_CONVERGED_INNER : (int)NMC_NONFINITE);
