@@ -145,6 +145,22 @@ def compute_opacities(grid, tables, rho, T, Ye, scale, proc_mask, dmin, dmax):
         for s in range(ns):
             sb = s ^ 1
             phi_pro[s], phi_ann[s] = pair_kernels(scale[3] * ann[s // 2], deq[s], deq[sb], s % 2 == 0)
-    return dict(T=T, mu_e=mu_e, eta_e=eta_e, mu=mus, deq=deq, chi_ab=chi_ab, sig=sig,
-                phi_in=phi_in, phi_out=phi_out, phi_pro=phi_pro, phi_ann=phi_ann,
-                clamped=bool(c1 or c2 or c3 or c4))
+    op = dict(T=T, mu_e=mu_e, eta_e=eta_e, mu=mus, deq=deq, chi_ab=chi_ab, sig=sig,
+              phi_in=phi_in, phi_out=phi_out, phi_pro=phi_pro, phi_ann=phi_ann,
+              clamped=bool(c1 or c2 or c3 or c4))
+    if "nes1" in tables:
+        # linear-order kernels (Eqs. linearCorrectionsNES, linearCorrectionsPair); reading: they obey
+        # the in-out invariance and detailed-balance relations of the isotropic ones, which hold for
+        # every Legendre coefficient of a kernel, and take the same scale factors
+        for key in ("phi1_in", "phi1_out", "phi1_pro", "phi1_ann"):
+            op[key] = np.zeros((ns, ne, ne))
+        if proc_mask & NES:
+            lower1, _ = interpolate_kernel(tables["nes1"], tables, T, eta_e)
+            for s in range(ns):
+                op["phi1_out"][s], op["phi1_in"][s] = nes_kernels(scale[2] * lower1[s], deq[s])
+        if proc_mask & PAIR:
+            ann1, _ = interpolate_kernel(tables["pair1"], tables, T, eta_e)
+            for s in range(ns):
+                op["phi1_pro"][s], op["phi1_ann"][s] = pair_kernels(scale[3] * ann1[s // 2], deq[s], deq[s ^ 1],
+                                                                    s % 2 == 0)
+    return op

@@ -93,11 +93,38 @@ def moment_map(M, U_star, op, W2, dtau, v):
     kappa = chi + op["sig"]                                  # Eq. transportOpacityNodal
     lam = 1.0 / (1.0 + math.sqrt(float(v @ v)))
     N_star, G_star = U_star
+    cD, cI = linear_corrections(M, op, W2) if "phi1_in" in op else (0.0, 0.0)
     Q = np.empty_like(M)
-    Q[:, :, 0] = ((1.0 - lam) * D + lam * (N_star - I @ v + dtau * eta)) / (1.0 + lam * dtau * chi)
+    Q[:, :, 0] = ((1.0 - lam) * D + lam * (N_star - I @ v + dtau * (eta + cD))) / (1.0 + lam * dtau * chi)
     vK = np.einsum("i,...ij->...j", v, rank2(M))
-    Q[:, :, 1:] = ((1.0 - lam) * I + lam * (G_star - vK)) / (1.0 + lam * dtau * kappa)[:, :, None]
+    Q[:, :, 1:] = ((1.0 - lam) * I + lam * (G_star - vK + dtau * cI)) / (1.0 + lam * dtau * kappa)[:, :, None]
     return Q
+
+
+def linear_corrections(M, op, W2):
+    """Linear-order NES and pair terms of the moment equations (Eqs. zerothMomentCollisionTerm_NES,
+    firstMomentCollisionTerm_NES, zerothMomentCollisionTerm_Pair, firstMomentCollisionTerm_Pair) with
+    <Phi_1 I> of Eqs. linearCorrectionsNES and linearCorrectionsPair by the energy quadrature:
+        number: -(A_in - A_out).I + (P_pro - P_ann).I
+        flux_j: (1/3)(gamma_ij - 3 K_ij) A_in^i + K_ij A_out^i
+                - (1/3)(gamma_ij - 3 K_ij) P_pro^i - K_ij P_ann^i,
+    A = <Phi_1^{In/Out} I_s>, P = <Phi_1^{Pro/Ann} I_sbar>, K = k D.  Returns (cD (ns, ne), cI (ns, ne, 3)).
+    Reading: they enter Eq. implicitMomentsNodal as explicit additions to dtau eta and to the flux
+    numerator, evaluated at the current iterate."""
+    D, I = M[:, :, 0], M[:, :, 1:]
+    ns = D.shape[0]
+    K = rank2(M)
+    cD = np.zeros_like(D)
+    cI = np.zeros_like(I)
+    for s in range(ns):
+        sb = s ^ 1
+        wI, wIb = W2[:, None] * I[s], W2[:, None] * I[sb]
+        A_in, A_out = op["phi1_in"][s] @ wI, op["phi1_out"][s] @ wI
+        P_pro, P_ann = op["phi1_pro"][s] @ wIb, op["phi1_ann"][s] @ wIb
+        cD[s] = -np.sum((A_in - A_out) * I[s], axis=-1) + np.sum((P_pro - P_ann) * I[s], axis=-1)
+        KA = lambda A: np.einsum("qij,qi->qj", K[s], A)  # noqa: E731
+        cI[s] = (A_in / 3.0 - KA(A_in)) + KA(A_out) - (P_pro / 3.0 - KA(P_pro)) - KA(P_ann)
+    return cD, cI
 
 
 def eulerian_sums(M, v, grid, g):

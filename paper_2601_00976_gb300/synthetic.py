@@ -52,8 +52,9 @@ def _species_list(ns):
     return [min(s, 2 + (s % 2)) for s in range(ns)]   # 0 nue, 1 anue, heavy -> 2/3
 
 
-def make_tables(energies, ns, seed=0):
-    """Synthetic opacity and kernel tables for nodal energies `energies` (MeV)."""
+def make_tables(energies, ns, seed=0, linear=False):
+    """Synthetic opacity and kernel tables for nodal energies `energies` (MeV); with `linear`, also
+    the linear-order kernels Phi_1 of NES and pair ("nes1", "pair1", drawn after the others)."""
     rng = np.random.default_rng(seed)
     en = np.asarray(energies, dtype=np.float64)
     ne = en.size
@@ -96,9 +97,22 @@ def make_tables(energies, ns, seed=0):
     for p in range(npair):
         amp = PAIR0[min(p, 1)] * dens * np.exp(-0.1 * ket)[None, :] * _smooth_factor(rng, XK, XE)
         pair[p] = amp[:, :, None, None] * pshape[None, None, :, :]
-    return dict(ns=ns, ne=ne, energies=en.copy(),
-                lrho=RHO_AXIS, lT=T_AXIS, ye=YE_AXIS, emab=emab, iso=iso,
-                klT=KT_AXIS, keta=KETA_AXIS, nes=nes, pair=pair)
+    out = dict(ns=ns, ne=ne, energies=en.copy(),
+               lrho=RHO_AXIS, lT=T_AXIS, ye=YE_AXIS, emab=emab, iso=iso,
+               klT=KT_AXIS, keta=KETA_AXIS, nes=nes, pair=pair)
+    if linear:
+        # linear-order Legendre coefficients Phi_1 of the same kernels: Phi_1 = -c Phi_0 with c a
+        # seeded smooth function of (log T, eta) in [0.1, 0.4] (|Phi_1| < Phi_0, a kernel that
+        # stays positive over scattering angles)
+        out["nes1"] = np.empty_like(nes)
+        for s in range(ns):
+            c = 0.25 * _smooth_factor(rng, XK, XE, amp=math.log(1.6))
+            out["nes1"][s] = -c[:, :, None, None] * nes[s]
+        out["pair1"] = np.empty_like(pair)
+        for p_ in range(npair):
+            c = 0.25 * _smooth_factor(rng, XK, XE, amp=math.log(1.6))
+            out["pair1"][p_] = -c[:, :, None, None] * pair[p_]
+    return out
 
 
 def _logistic(e, a, T):
