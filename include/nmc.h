@@ -122,6 +122,15 @@ typedef struct {
     double eta_min, eta_max;     /* eta_e */
     const double* nes;
     const double* pair;
+    /* Optional linear-order (Legendre l = 1) kernels Phi_1 of NES and pair, laid
+     * out as nes and pair (both or neither; NULL: none).  Only collision_solve_v
+     * reads them: the linear corrections of Eqs. zerothMomentCollisionTerm_NES,
+     * firstMomentCollisionTerm_NES, zerothMomentCollisionTerm_Pair and
+     * firstMomentCollisionTerm_Pair, with <Phi_1 I> of Eqs.
+     * linearCorrectionsNES and linearCorrectionsPair; Phi_1 is completed by the
+     * same in-out invariance and detailed balance as Phi_0. */
+    const double* nes1;
+    const double* pair1;
 } nmc_tables;
 
 /* Solver parameters (Algorithm 1 parameters plus the readings the paper leaves open). */

@@ -192,6 +192,7 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
         if (!(grid->edges[i + 1] > grid->edges[i]) || !std::isfinite(grid->edges[i + 1])) return NMC_EINVAL;
     if (!(grid->edges[0] >= 0.0)) return NMC_EINVAL;
     if (!tb->emab || !tb->iso || !tb->nes || !tb->pair) return NMC_EINVAL;
+    if ((tb->nes1 == nullptr) != (tb->pair1 == nullptr)) return NMC_EINVAL;
     if (!axis_ok(tb->lrho_min, tb->lrho_max, tb->n_rho) || !axis_ok(tb->lt_min, tb->lt_max, tb->n_t) ||
         !axis_ok(tb->ye_min, tb->ye_max, tb->n_ye) || !axis_ok(tb->klt_min, tb->klt_max, tb->n_kt) ||
         !axis_ok(tb->eta_min, tb->eta_max, tb->n_eta))
@@ -314,6 +315,13 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
     if (rc == NMC_OK) rc = upload(ctx, tb->iso, n_op, &t.iso);
     if (rc == NMC_OK) rc = upload(ctx, tb->nes, n_nes, &t.nes);
     if (rc == NMC_OK) rc = upload(ctx, tb->pair, n_pair, &t.pair);
+    // linear-order kernels (optional, both or neither; read by the O(v/c) solve)
+    t.nes1 = nullptr;
+    t.pair1 = nullptr;
+    if (rc == NMC_OK && tb->nes1 && tb->pair1) {
+        rc = upload(ctx, tb->nes1, n_nes, &t.nes1);
+        if (rc == NMC_OK) rc = upload(ctx, tb->pair1, n_pair, &t.pair1);
+    }
     // FP32 copies for the mixed path; kernel tables prescaled by 4 pi / (hc)^3
     if (rc == NMC_OK) rc = upload_f32(ctx, tb->emab, n_op, 1.0, &t.emab_f);
     if (rc == NMC_OK) rc = upload_f32(ctx, tb->iso, n_op, 1.0, &t.iso_f);

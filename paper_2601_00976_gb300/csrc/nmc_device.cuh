@@ -435,6 +435,8 @@ struct OpacBufs {
     R* vAi;    //           1 / a
     R* vDeq;   //           D^Eq
     R* vDeqc;  //           1 - D^Eq (mixed precision; FP64 forms it from D^Eq)
+    R* phi1 = nullptr;   // linear-order NES kernels K_1,Out (as phi), filled when the tables have them
+    R* ann1 = nullptr;   // linear-order pair kernels K_1,Ann (as ann)
 };
 
 // ComputeOpacities of Algorithm 1 at the matter state (rho, T, Ye), called by
@@ -641,63 +643,66 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         const R w01 = ((R)1 - kt) * ke, w11 = kt * ke;
         const long long mat = (long long)NE * NE;
         const long long sE = mat, sT = (long long)tb.eta.n * mat;
-        if (nes_on && s < NS) {
-            const R c = kMixed ? (R)os->pre_f[2] : (R)os->pre[2];
-            const long long off = (((long long)s * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
-            R* P0 = b.phi + s * NE * LD;
-            // lower triangle incl. diagonal, entries enumerated row by row so that every lane of the
-            // species group has one (a row loop with q <= r leaves half the lanes idle)
-            const int ntri = NE * (NE + 1) / 2;
-            for (int idx = q; idx < ntri; idx += NEP) {
-                int r = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
-                while (r * (r + 1) / 2 > idx) --r;
-                while ((r + 1) * (r + 2) / 2 <= idx) ++r;
-                const int cc = idx - r * (r + 1) / 2;
-                const long long o = off + (long long)r * NE + cc;
-                R v;
-                if (kMixed) {
-                    const float* t = tb.nes_f;
-                    v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
-                } else {
-                    const double* t = tb.nes;
-                    v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
+        // lower NES triangle and the pair matrix of one kernel order (Phi_0, or Phi_1 in PH1/AN1)
+        auto fill = [&](const double* tn, const float* tnf, const double* tp, const float* tpf, R* PH, R* AN) {
+            if (nes_on && s < NS) {
+                const R c = kMixed ? (R)os->pre_f[2] : (R)os->pre[2];
+                const long long off = (((long long)s * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
+                R* P0 = PH + s * NE * LD;
+                // lower triangle incl. diagonal, entries enumerated row by row so that every lane of the
+                // species group has one (a row loop with q <= r leaves half the lanes idle)
+                const int ntri = NE * (NE + 1) / 2;
+                for (int idx = q; idx < ntri; idx += NEP) {
+                    int r = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
+                    while (r * (r + 1) / 2 > idx) --r;
+                    while ((r + 1) * (r + 2) / 2 <= idx) ++r;
+                    const int cc = idx - r * (r + 1) / 2;
+                    const long long o = off + (long long)r * NE + cc;
+                    R v;
+                    if (kMixed) v = w00 * tnf[o] + w10 * tnf[o + sT] + w01 * tnf[o + sE] + w11 * tnf[o + sT + sE];
+                    else v = w00 * tn[o] + w10 * tn[o + sT] + w01 * tn[o + sE] + w11 * tn[o + sT + sE];
+                    P0[r * LD + cc] = c * v;
                 }
-                P0[r * LD + cc] = c * v;
             }
-        }
-        if (pair_on && s < NS) {
-            const int pr = s >> 1;
-            const R c = kMixed ? (R)os->pre_f[3] : (R)os->pre[3];
-            const long long off = (((long long)pr * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
-            R* A0 = b.ann + pr * NE * LD;
-            for (int idx = (s & 1) * NEP + q; idx < NE * NE; idx += 2 * NEP) {
-                const int r = idx / NE, cc = idx - r * NE;
-                const long long o = off + idx;
-                R v;
-                if (kMixed) {
-                    const float* t = tb.pair_f;
-                    v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
-                } else {
-                    const double* t = tb.pair;
-                    v = w00 * t[o] + w10 * t[o + sT] + w01 * t[o + sE] + w11 * t[o + sT + sE];
+            if (pair_on && s < NS) {
+                const int pr = s >> 1;
+                const R c = kMixed ? (R)os->pre_f[3] : (R)os->pre[3];
+                const long long off = (((long long)pr * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
+                R* A0 = AN + pr * NE * LD;
+                for (int idx = (s & 1) * NEP + q; idx < NE * NE; idx += 2 * NEP) {
+                    const int r = idx / NE, cc = idx - r * NE;
+                    const long long o = off + idx;
+                    R v;
+                    if (kMixed) v = w00 * tpf[o] + w10 * tpf[o + sT] + w01 * tpf[o + sE] + w11 * tpf[o + sT + sE];
+                    else v = w00 * tp[o] + w10 * tp[o + sT] + w01 * tp[o + sE] + w11 * tp[o + sT + sE];
+                    A0[r * LD + cc] = c * v;
                 }
-                A0[r * LD + cc] = c * v;
             }
-        }
+        };
+        fill(tb.nes, tb.nes_f, tb.pair, tb.pair_f, b.phi, b.ann);
+        // linear-order kernels: the same interpolation, scale factors and relations (in-out invariance,
+        // detailed balance) as the isotropic ones
+        const bool lin = !kMixed && b.phi1 != nullptr && tb.nes1 != nullptr;
+        if (lin) fill(tb.nes1, nullptr, tb.pair1, nullptr, b.phi1, b.ann1);
         __syncthreads();
-        if (nes_on && s < NS) {   // up-scattering by detailed balance: K[r][c] = a_c / a_r K[c][r], r < c
-            R* P0 = b.phi + s * NE * LD;
-            const R* va = b.vA + s * NEP;
-            const R* vai = b.vAi + s * NEP;
-            const int nup = NE * (NE - 1) / 2;   // strictly upper entries, column by column
-            for (int idx = q; idx < nup; idx += NEP) {
-                int cc = (int)((sqrtf(8.0f * idx + 1.0f) + 1.0f) * 0.5f);
-                while (cc * (cc - 1) / 2 > idx) --cc;
-                while ((cc + 1) * cc / 2 <= idx) ++cc;
-                const int r = idx - cc * (cc - 1) / 2;
-                P0[r * LD + cc] = va[cc] * vai[r] * P0[cc * LD + r];
+        // up-scattering by detailed balance: K[r][c] = a_c / a_r K[c][r], r < c
+        auto upper = [&](R* PH) {
+            if (nes_on && s < NS) {
+                R* P0 = PH + s * NE * LD;
+                const R* va = b.vA + s * NEP;
+                const R* vai = b.vAi + s * NEP;
+                const int nup = NE * (NE - 1) / 2;   // strictly upper entries, column by column
+                for (int idx = q; idx < nup; idx += NEP) {
+                    int cc = (int)((sqrtf(8.0f * idx + 1.0f) + 1.0f) * 0.5f);
+                    while (cc * (cc - 1) / 2 > idx) --cc;
+                    while ((cc + 1) * cc / 2 <= idx) ++cc;
+                    const int r = idx - cc * (cc - 1) / 2;
+                    P0[r * LD + cc] = va[cc] * vai[r] * P0[cc * LD + r];
+                }
             }
-        }
+        };
+        upper(b.phi);
+        if (lin) upper(b.phi1);
     }
     __syncthreads();
 }

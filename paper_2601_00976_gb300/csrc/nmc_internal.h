@@ -67,6 +67,8 @@ struct DevTables {
     const double* iso;
     const double* nes;     // [ns][nkt][neta][ne][ne]
     const double* pair;    // [ns/2][nkt][neta][ne][ne]
+    const double* nes1;    // linear-order (Phi_1) NES table, as nes, or null
+    const double* pair1;   // linear-order (Phi_1) pair table, as pair, or null
     // FP32 copies for the mixed-precision kernel; kernels prescaled by 4 pi / (hc)^3
     const float* emab_f;
     const float* iso_f;

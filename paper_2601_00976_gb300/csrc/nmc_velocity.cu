@@ -10,6 +10,9 @@
 //      D <- ((1 - lam) D + lam (N* - v.I + dtau eta)) / (1 + lam dtau chi),
 //      I_j <- ((1 - lam) I_j + lam (G*_j - v^i K_ij)) / (1 + lam dtau kappa),
 //    with lam = 1 / (1 + |v|) and v the velocity of the current matter iterate;
+//  - with linear-order (Phi_1) kernels in the tables, their NES and pair terms
+//    (Eqs. zerothMomentCollisionTerm_NES/Pair, firstMomentCollisionTerm_NES/Pair)
+//    as explicit additions to dtau eta and to the flux numerator;
 //  - the matter map q of Eq. implicitFluidNodal: momentum, total specific
 //    energy eps_f and Ye from the Eulerian sums F_nu, E_nu, N_nu
 //    (Eqs. eulerianMomentumLG, eulerianEnergyLG, eulerianNumberLG), the
@@ -156,6 +159,8 @@ struct VelArgs {
     int freeze;
     double v_floor;
     int off_red, off_node;
+    int linear;                      // the tables carry linear-order (Phi_1) kernels
+    int off_phi1, off_ann1, off_wI;  // their matrices and the W~ I vectors (linear only)
 };
 
 template <int MAXT, int MINB>
@@ -180,7 +185,11 @@ __global__ void __launch_bounds__(MAXT, MINB) velocity_kernel(const VelArgs va) 
     double* vDeqc = vDeq + NS * NEP;
     void* red = smb + va.off_red;
     VelNode* nd = reinterpret_cast<VelNode*>(smb + va.off_node);
-    const OpacBufs<double> ob{phi, ann, vA, vAi, vDeq, vDeqc};
+    const bool lin = va.linear != 0;
+    double* phi1 = lin ? reinterpret_cast<double*>(smb + va.off_phi1) : nullptr;   // [NS][NE][LD] K_1,Out
+    double* ann1 = lin ? reinterpret_cast<double*>(smb + va.off_ann1) : nullptr;   // [NS/2][NE][LD] K_1,Ann
+    double* vWI = lin ? reinterpret_cast<double*>(smb + va.off_wI) : nullptr;      // [3][NS][NEP] W~ I^c
+    const OpacBufs<double> ob{phi, ann, vA, vAi, vDeq, vDeqc, phi1, ann1};
 
     const nmc_params& P = a.p;
     const bool nes_on = (P.proc_mask & NMC_PROC_NES) != 0;
@@ -294,14 +303,16 @@ __global__ void __launch_bounds__(MAXT, MINB) velocity_kernel(const VelArgs va) 
                     }
                 }
             }
-            auto publish = [&](const double D) {
+            auto publish = [&](const double (&Mv)[4]) {
                 if (act) {
-                    vWD[sq] = Wt * D;
-                    vW1D[sq] = Wt * (1.0 - D);
-                    vAW1D[sq] = vA[sq] * Wt * (1.0 - D);
+                    vWD[sq] = Wt * Mv[0];
+                    vW1D[sq] = Wt * (1.0 - Mv[0]);
+                    vAW1D[sq] = vA[sq] * Wt * (1.0 - Mv[0]);
+                    if (lin)
+                        for (int c = 0; c < 3; ++c) vWI[c * NS * NEP + sq] = Wt * Mv[1 + c];
                 }
             };
-            publish(M[0]);
+            publish(M);
             __syncthreads();
             bool inner_stop = false;
             for (int ell = 1;; ++ell) {
@@ -338,10 +349,56 @@ __global__ void __launch_bounds__(MAXT, MINB) velocity_kernel(const VelArgs va) 
                     double aa, cc;
                     closure_ac(M[0], M[1], M[2], M[3], aa, cc);
                     const double vI = vk[0] * M[1] + vk[1] * M[2] + vk[2] * M[3];
-                    Qv[0] = ((1.0 - lam) * M[0] + lam * (Nst - vI + eta)) / (1.0 + lam * chi);
+                    double cD = 0.0, cI[3] = {0.0, 0.0, 0.0};
+                    if (lin) {
+                        // linear-order NES and pair terms (Eqs. zerothMomentCollisionTerm_NES/Pair,
+                        // firstMomentCollisionTerm_NES/Pair), explicit at the current iterate:
+                        // A = <Phi_1^{In,Out} I_s>, P = <Phi_1^{Pro,Ann} I_sbar> (Eqs.
+                        // linearCorrectionsNES/Pair), K_ij = aa delta_ij + cc I_i I_j
+                        double Ai[3] = {0, 0, 0}, Ao[3] = {0, 0, 0}, Pp[3] = {0, 0, 0}, Pa[3] = {0, 0, 0};
+                        if (nes_on) {
+                            const double* P1 = phi1 + s * NE * LD;
+                            for (int j = 0; j < NE; ++j) {
+                                const double kin = P1[j * LD + q], kout = P1[q * LD + j];
+                                for (int c = 0; c < 3; ++c) {
+                                    const double wi = vWI[c * NS * NEP + s * NEP + j];
+                                    Ai[c] = fma(kin, wi, Ai[c]);
+                                    Ao[c] = fma(kout, wi, Ao[c]);
+                                }
+                            }
+                        }
+                        if (pair_on) {
+                            const int pt = s ^ 1;
+                            const double* A1 = ann1 + (s >> 1) * NE * LD;
+                            const int stride_j = (s & 1) == 0 ? 1 : LD;
+                            const int base = (s & 1) == 0 ? q * LD : q;
+                            for (int j = 0; j < NE; ++j) {
+                                const double av = A1[base + j * stride_j];
+                                const double ab = vA[pt * NEP + j];
+                                for (int c = 0; c < 3; ++c) {
+                                    const double wi = vWI[c * NS * NEP + pt * NEP + j];
+                                    Pa[c] = fma(av, wi, Pa[c]);
+                                    Pp[c] = fma(av, ab * wi, Pp[c]);
+                                }
+                            }
+                            for (int c = 0; c < 3; ++c) Pp[c] *= vA[sq];
+                        }
+                        auto IdotX = [&](const double* X) { return M[1] * X[0] + M[2] * X[1] + M[3] * X[2]; };
+                        cD = -(IdotX(Ai) - IdotX(Ao)) + (IdotX(Pp) - IdotX(Pa));
+                        const double iAi = IdotX(Ai), iAo = IdotX(Ao), iPp = IdotX(Pp), iPa = IdotX(Pa);
+                        for (int c = 0; c < 3; ++c) {
+                            // (K X)_c = aa X_c + cc (I.X) I_c
+                            const double KAi = aa * Ai[c] + cc * iAi * M[1 + c];
+                            const double KAo = aa * Ao[c] + cc * iAo * M[1 + c];
+                            const double KPp = aa * Pp[c] + cc * iPp * M[1 + c];
+                            const double KPa = aa * Pa[c] + cc * iPa * M[1 + c];
+                            cI[c] = (Ai[c] / 3.0 - KAi) + KAo - (Pp[c] / 3.0 - KPp) - KPa;
+                        }
+                    }
+                    Qv[0] = ((1.0 - lam) * M[0] + lam * (Nst - vI + eta + cD)) / (1.0 + lam * chi);
                     const double rI = 1.0 / (1.0 + lam * kap);
                     for (int j = 0; j < 3; ++j)
-                        Qv[1 + j] = ((1.0 - lam) * M[1 + j] + lam * (Gst[j] - (aa * vk[j] + cc * vI * M[1 + j]))) * rI;
+                        Qv[1 + j] = ((1.0 - lam) * M[1 + j] + lam * (Gst[j] - (aa * vk[j] + cc * vI * M[1 + j]) + cI[j])) * rI;
                     for (int c = 0; c < 4; ++c) F[c] = Qv[c] - M[c];
                 }
                 for (int j = 0; j < 2; ++j)
@@ -374,7 +431,7 @@ __global__ void __launch_bounds__(MAXT, MINB) velocity_kernel(const VelArgs va) 
                         if (j >= 3 - m) acc = fma(nd->alpha[j], Qh[j][c], acc);
                     Mn[c] = act ? acc : 0.0;
                 }
-                publish(Mn[0]);
+                publish(Mn);
                 int vote = 1;
                 {   // Algorithm 2
                     double v[4];
@@ -572,7 +629,18 @@ int launch_velocity(nmc_ctx* ctx, const SolveArgs& a, const double* v_in, double
     const size_t b_node = (sizeof(VelNode) + 15) / 16 * 16;
     va.off_red = va.a.off_red;   // replace the fused kernel's reduction and node carve
     va.off_node = (int)(va.a.off_red + b_red);
-    const size_t smem = (size_t)va.off_node + b_node;
+    size_t smem = (size_t)va.off_node + b_node;
+    va.linear = (ctx->tb.nes1 != nullptr && ctx->tb.pair1 != nullptr) ? 1 : 0;
+    if (va.linear) {
+        const size_t LDb = (size_t)(ctx->ne + 1);
+        const size_t b_phi1 = ((size_t)ctx->ns * ctx->ne * LDb * sizeof(double) + 15) / 16 * 16;
+        const size_t b_ann1 = ((size_t)(ctx->ns / 2) * ctx->ne * LDb * sizeof(double) + 15) / 16 * 16;
+        const size_t b_wI = ((size_t)3 * ctx->ns * ctx->nep * sizeof(double) + 15) / 16 * 16;
+        va.off_phi1 = (int)smem;
+        va.off_ann1 = (int)(smem + b_phi1);
+        va.off_wI = (int)(smem + b_phi1 + b_ann1);
+        smem += b_phi1 + b_ann1 + b_wI;
+    }
     (void)base;
     if ((int)smem > ctx->max_smem_optin)
         return set_error(ctx, NMC_EUNSUPPORTED, "shared-memory footprint of the velocity kernel exceeds the per-block limit");

@@ -41,7 +41,8 @@ class Tables(ctypes.Structure):
                 ("n_kt", ctypes.c_int32), ("n_eta", ctypes.c_int32),
                 ("klt_min", ctypes.c_double), ("klt_max", ctypes.c_double),
                 ("eta_min", ctypes.c_double), ("eta_max", ctypes.c_double),
-                ("nes", _c_double_p), ("pair", _c_double_p)]
+                ("nes", _c_double_p), ("pair", _c_double_p),
+                ("nes1", _c_double_p), ("pair1", _c_double_p)]
 
 
 class Params(ctypes.Structure):
@@ -157,7 +158,7 @@ class Context:
         self._lib = load_library()
         self._keep = [_dptr(edges)]
         g = Grid(len(edges) - 1, n_q, n_species, self._keep[0].ctypes.data_as(_c_double_p))
-        arrs = {k: _dptr(tables[k]) for k in ("emab", "iso", "nes", "pair")}
+        arrs = {k: _dptr(tables[k]) for k in ("emab", "iso", "nes", "pair", "nes1", "pair1") if k in tables}
         self._keep += list(arrs.values())
         t = Tables()
         t.n_rho, t.n_t, t.n_ye = tables["lrho"][2], tables["lT"][2], tables["ye"][2]

@@ -17,13 +17,13 @@ from paper_2601_00976_gb300 import synthetic
 _TABLES = {}
 
 
-def _grid_tables(n_elem, de1, nq, ns, table_seed):
-    key = (n_elem, de1, nq, ns, table_seed)
+def _grid_tables(n_elem, de1, nq, ns, table_seed, linear=False):
+    key = (n_elem, de1, nq, ns, table_seed, linear)
     if key not in _TABLES:
         edges, _ = ogrid.geometric_edges(n_elem, de1)
         g = ogrid.EnergyGrid(edges, nq)
         _TABLES.clear()
-        _TABLES[key] = (g, synthetic.make_tables(g.eps, ns, seed=table_seed))
+        _TABLES[key] = (g, synthetic.make_tables(g.eps, ns, seed=table_seed, linear=linear))
     return _TABLES[key]
 
 
