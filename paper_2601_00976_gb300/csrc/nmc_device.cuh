@@ -345,7 +345,8 @@ __device__ __forceinline__ double gram3_update_warp(double (*G)[LDG], double nr,
     return ((u - G[gi][L]) - w) + z;
 }
 
-// Outer least squares on the 2-component scaled residuals (thread 0 only).
+// Outer least squares on the 2-component scaled residuals, by one thread (windows deeper than 3;
+// outer_step_warp handles depth <= 3 lane-parallel).
 __device__ inline void outer_anderson(const double (&fh)[kMaxOuterMem][2], int m, double* beta) {
     constexpr int MM = kMaxOuterMem;
     double G[MM][MM];
@@ -411,7 +412,7 @@ __device__ inline void outer_step_warp(double (*qh)[2], double (*fh)[2], double 
 
 
 // Node-wide results of the scalar part of ComputeOpacities (shared memory,
-// written by thread 0).
+// written by lane 0 of the lead warp).
 struct OpacState {
     double eta_e;              // mu_e / T
     double mu[kMaxSpecies];    // neutrino chemical potentials per species
@@ -442,7 +443,8 @@ struct OpacBufs {
 // ComputeOpacities of Algorithm 1 at the matter state (rho, T, Ye), called by
 // every thread of the block with the same arguments (sc points to the node's
 // four scale factors EmAb, Iso, NES, Pair).
-//  - Chemical potentials from the EoS (thread 0; FP32 in mixed precision).
+//  - Chemical potentials from the EoS (the lead warp; an FP32 root refined in FP64 in mixed
+//    precision).
 //  - Fermi--Dirac values at the projection quadrature points, the
 //    eps^2-weighted L2 projection and the bound-enforcing limiter per
 //    (species, element) (Eq. fermiDiracProjection).

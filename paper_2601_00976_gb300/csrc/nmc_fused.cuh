@@ -3,8 +3,10 @@
 //   R = double  every step in FP64;
 //   R = float   mixed: table interpolation, D^Eq, kernel contractions and the
 //               fixed-point sweeps (map Q, residuals, Anderson mixing, Gram
-//               sums, Algorithm 2) in FP32; conservation sums, matter update,
-//               the Anderson least-squares solves and the final EoS step in FP64.
+//               sums, Algorithm 2) in FP32, the number moment and the map's
+//               numerator as double-floats (two FP32 words); conservation
+//               sums, matter update, the Anderson least-squares solves and the
+//               final EoS step in FP64.
 //
 // Mapping.  One thread block solves one spatial node at a time; blocks are
 // persistent and take node indices from a device work queue (an atomic
@@ -35,13 +37,13 @@
 // Per inner iteration: rates as shared-memory mat-vecs (Phi_In = Phi_Out^T;
 // the antiparticle's Phi_Ann is the transpose; Phi_Pro = a_s(q) a_sbar(q')
 // Phi_Ann with a = D/(1-D) by Eq. detailedBalancePair), the map Q
-// (Eq. implicitMomentsNodal, v = 0), one block reduction for the new row of the
-// Anderson Gram matrix, the least-squares solve in thread 0 (FP64), the mixing
-// update, and a per-species reduction for Algorithm 2.
+// (Eq. implicitMomentsNodal, v = 0), one block reduction for the Anderson
+// least-squares entries, the least-squares solve by the lead warp (FP64,
+// lane-parallel), the mixing update, and the Algorithm 2 vote; three barriers.
 //
 // Matter update (Eq. implicitFluidNodal with Eqs. eulerianEnergyLG,
 // eulerianNumberLG): one FP64 block reduction for E_nu and N_nu, the outer
-// Anderson step and Algorithm 3 in thread 0, then T by EoS root finding.
+// Anderson step and Algorithm 3 on the lead warp, then T by EoS root finding.
 #pragma once
 
 #include <cuda_runtime.h>
