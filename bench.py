@@ -19,7 +19,9 @@ launches (NMC_MODE_PLAIN) on the same inputs; 2^17 nodes by default,
 --batching-nodes 4194304 for the full 2^22-node configuration; and a
 "velocity" object: collision_solve_v (the O(v/c) solve with the momentum
 update, FP64) over 2^16 nodes of the profile with an infall velocity field;
-and a "c2p" object: conserved_to_primitive over every bin of 2^16 nodes.
+a "c2p" object: conserved_to_primitive over every bin of 2^16 nodes; and a
+"relaxation" object: the relaxation problem of Sec. 6.1 through the
+backward-Euler driver, batched over 4096 perturbed problems.
 
 Prints one JSON line.  --impl reference times the CPU oracle (the plain FP64
 restatement of the algorithm) on a bounded sample of the same workload.
@@ -60,6 +62,9 @@ FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64: 152 SMs x 4 flop/clk x 2.07 GHz 
 CPU_SAMPLE = 48           # oracle sample (nodes) for the CPU baseline
 ADJ_NODES = 1 << 18
 BATCH_NODES = 1 << 17
+REL_WORKLOAD = ("relaxation problem of Sec. 6.1 (six species, Grid C 16x2, v = 0.1 c, Gaussian forward-peaked "
+                "initial neutrinos), +-10% seeded perturbations of rho = 1e12, T = 7.6 MeV, Ye = 0.135 per problem, "
+                "backward Euler with dt from 1e-4 ms x1.04 per step to t = 100 ms, tol 1e-8, Anderson depth 2")
 C2P_WORKLOAD = ("conserved-to-primitive recovery of every bin (collapse profile, 2^16 nodes x 4 species x 32 "
                 "energies, conserved moments of the profile's occupations, infall velocity up to 0.15 c), FP64, "
                 "tol 1e-8, Anderson memory 3")
@@ -85,10 +90,20 @@ def _args():
                     help="nodes of the O(v/c) solve measurement (0 skips it)")
     ap.add_argument("--c2p-nodes", type=int, default=N_NODES,
                     help="nodes of the conserved-to-primitive measurement (0 skips it)")
+    ap.add_argument("--relaxation-problems", type=int, default=4096,
+                    help="problems in the relaxation-driver measurement (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="path reported as the headline value (both are timed)")
     return ap.parse_args()
+
+
+def _grid():
+    """Interfaces and node energies of Grid C with linear elements, from the library."""
+    from paper_2601_00976_gb300 import nmc
+    edges, _ = nmc.geometric_edges(N_ELEM, DE1)
+    eps, _, _ = nmc.grid_nodes(edges, NQ)
+    return edges, eps
 
 
 def _workload(seed, nodes, oracle_grid=False):
@@ -269,6 +284,28 @@ def time_velocity(args, ctx, eps, dev, rank, barrier, allmax, stream):
     fl = float(np.sum(flops.velocity_node_flops(NS, len(eps), N_ELEM, NQ, MEM, n_in, n_out)))
     ach = fl / (kern_ms * 1e-3) / 1e12
     vmag = torch.sqrt((v * v).sum(1))
+    # the same solve with linear-order (Phi_1) NES and pair kernels in the tables
+    edges, _ = _grid()
+    tl = synthetic.make_tables(ctx.energies, NS, seed=0, linear=True)
+    ctx_l = nmc.Context(edges, NQ, NS, tl)
+    out_l = ctx_l.collision_solve_v(p, t["rho"], t["T"], t["Ye"], v, t["D"], t["I"], t["dt"], t["scale"])
+    for _ in range(args.warmup):
+        ctx_l.collision_solve_v(p, t["rho"], t["T"], t["Ye"], v, t["D"], t["I"], t["dt"], t["scale"], out=out_l)
+    barrier()
+    evl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evl[k][0].record(stream)
+        ctx_l.collision_solve_v(p, t["rho"], t["T"], t["Ye"], v, t["D"], t["I"], t["dt"], t["scale"], out=out_l)
+        evl[k][1].record(stream)
+    barrier()
+    total_l = allmax(evl[0][0].elapsed_time(evl[-1][1]))
+    linear = {"value": weak_scaling_value(ws * n, args.steps, total_l), "unit": "solves/s",
+              "ms_per_step": total_l / args.steps,
+              "converged_fraction": float((out_l["status"] == 0).float().mean().item()),
+              "mean_inner_iters": float(out_l["n_inner"].float().mean().item()),
+              "note": "tables with linear-order (Phi_1) NES and pair kernels; the kernel holds their matrices "
+                      "next to the isotropic ones (one block per SM)"}
+    ctx_l.close()
     return {"metric": "converged O(v/c) collision solves/s (nodes*steps/s)",
             "value": weak_scaling_value(ws * n, args.steps, total_ms), "unit": "solves/s",
             "ms_per_step": total_ms / args.steps, "dtype": "f64",
@@ -278,7 +315,51 @@ def time_velocity(args, ctx, eps, dev, rank, barrier, allmax, stream):
             "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": ach / FP64_PEAK_TFLOPS, "traffic": _traffic("velocity_kernel", n),
                          "kernel": "velocity_kernel", "peak_source": "derived FP64 FMA rate at 2.07 GHz",
-                         "algorithmic_flops_per_launch": fl, "kernel_ms": kern_ms}}
+                         "algorithmic_flops_per_launch": fl, "kernel_ms": kern_ms},
+            "linear_phi1": linear}
+
+
+def time_relaxation(args, dev, rank, barrier, allmax):
+    """The relaxation problem of Sec. 6.1 (six species, v = 0.1 c, dt x1.04 per step to 100 ms: 271 steps),
+    batched over problems with seeded +-10% perturbations of (rho, T, Ye), through the backward-Euler driver."""
+    import torch
+    from paper_2601_00976_gb300 import nmc, synthetic, relaxation
+    from paper_2601_00976_gb300.dist import workload_seed
+    n = args.relaxation_problems
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    edges, eps = _grid()
+    tables = synthetic.make_tables(eps, 6, seed=81)
+    ctx = nmc.Context(edges, NQ, 6, tables)
+    rng = np.random.default_rng(workload_seed(rank, 5))
+    f64 = dict(dtype=torch.float64, device=dev)
+    rho = torch.tensor(1e12 * rng.uniform(0.9, 1.1, n), **f64)
+    T = torch.tensor(7.6 * rng.uniform(0.9, 1.1, n), **f64)
+    Ye = torch.tensor(0.135 * rng.uniform(0.9, 1.1, n), **f64)
+    v = torch.zeros((n, 3), **f64)
+    v[:, 0] = 0.1
+    D0, I0 = relaxation.initial_moments(ctx.energies, 6, 7.6)
+    D = torch.tensor(np.broadcast_to(D0, (n,) + D0.shape).copy(), **f64)
+    I = torch.tensor(np.broadcast_to(I0, (n,) + I0.shape).copy(), **f64)
+    p = nmc.default_params(tol_inner=1e-8, tol_outer=1e-8, m_inner=2, m_outer=2, max_inner=1000, max_outer=200)
+    steps = relaxation.schedule()
+    rel = relaxation.Relaxation(ctx, p, rho, T, Ye, v, D, I)
+    L0, E0 = rel.totals()
+    barrier()
+    t0 = time.perf_counter()
+    rel.run(steps)
+    torch.cuda.synchronize()
+    barrier()
+    wall = allmax(time.perf_counter() - t0)
+    L1, E1 = rel.totals()
+    ok = rel.state["status"] == 0
+    out = {"metric": "relaxation problem-steps/s (problems*steps/s)", "value": ws * n * len(steps) / wall,
+           "unit": "problem-steps/s", "s_per_run": wall, "dtype": "f64",
+           "config": {"workload": REL_WORKLOAD, "problems_per_gpu": n, "steps": len(steps),
+                      "converged_fraction_last_step": float(ok.float().mean().item()),
+                      "max_rel_change_total_lepton_number": float((torch.abs(L1 - L0) / torch.abs(L0)).max().item()),
+                      "max_rel_change_total_energy": float((torch.abs(E1 - E0) / torch.abs(E0)).max().item())}}
+    ctx.close()
+    return out
 
 
 def time_c2p(args, ctx, eps, dev, rank, barrier, allmax, stream):
@@ -498,6 +579,7 @@ def run_nmc(args):
 
     vel = time_velocity(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.velocity_nodes > 0 else None
     c2p = time_c2p(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.c2p_nodes > 0 else None
+    rlx = time_relaxation(args, dev, rank, barrier, allmax) if args.relaxation_problems > 0 else None
     adj = time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.adjoint_nodes > 0 else None
     bat = time_batching(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.batching_nodes > 0 else None
 
@@ -547,6 +629,8 @@ def run_nmc(args):
             line["velocity"] = vel
         if c2p is not None:
             line["c2p"] = c2p
+        if rlx is not None:
+            line["relaxation"] = rlx
         if adj is not None:
             line["adjoint"] = adj
         if bat is not None:

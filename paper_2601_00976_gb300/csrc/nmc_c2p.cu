@@ -40,20 +40,30 @@ struct C2pArgs {
     uint32_t* status;     // [n]
 };
 
-// g(M) of Eq. c2p_FP for one bin.  The flux factor h = |I| / D and the coefficient c ~ D / |I|^2
-// come from one reciprocal of D and one reciprocal square root of |I|^2: FP64 division and square
-// root are instruction sequences on the FP64 pipe, which bounds this kernel.
+// g(M) of Eq. c2p_FP for one bin.  K_ij = a delta_ij + c I_i I_j with Minerbo's psi: for
+// h = |I| / D < 1, 3 psi - 1 = (2/5)(3 - h + 3h^2) h^2 gives c = (3 - h + 3h^2) / (5 D), with no
+// division by |I|^2 (whose rounding residue would overflow once |I| decays into the denormals)
+// and one reciprocal of D; FP64 division and square root are instruction sequences on the FP64
+// pipe, which bounds this kernel.  At h >= 1, psi = 1 and c = D / |I|^2; D <= 0 gives K = (D/3) delta.
 __device__ __forceinline__ void c2p_map(const double (&M)[4], double N, const double* G, const double* v,
                                         double lam, double (&g)[4]) {
     const double In2 = M[1] * M[1] + M[2] * M[2] + M[3] * M[3];
-    const bool hasI = In2 > 0.0, hasD = M[0] > 0.0;
-    const double rIn = hasI ? rsqrt(In2) : 0.0;   // 1 / |I|
-    const double rD = hasD ? 1.0 / M[0] : 0.0;
-    double h = In2 * rIn * rD;
-    h = fmin(fmax(h, 0.0), 1.0);
-    const double psi = 1.0 / 3.0 + (2.0 / 15.0) * (3.0 - h + 3.0 * h * h) * h * h;
-    const double a = 0.5 * (1.0 - psi) * M[0];
-    const double c = 0.5 * (3.0 * psi - 1.0) * M[0] * rIn * rIn;
+    double a, c;
+    if (!(M[0] > 0.0)) {
+        a = M[0] / 3.0;
+        c = 0.0;
+    } else {
+        const double rD = 1.0 / M[0];
+        const double h = sqrt(In2) * rD;
+        if (h >= 1.0) {
+            a = 0.0;
+            c = M[0] / In2;
+        } else {
+            const double p = 3.0 - h + 3.0 * h * h;
+            a = 0.5 * (2.0 / 3.0 - (2.0 / 15.0) * p * h * h) * M[0];
+            c = 0.2 * p * rD;
+        }
+    }
     const double vI = v[0] * M[1] + v[1] * M[2] + v[2] * M[3];
     const double ml = 1.0 - lam;
     g[0] = ml * M[0] + lam * (N - vI);

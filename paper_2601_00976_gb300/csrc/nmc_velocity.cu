@@ -63,17 +63,28 @@ struct VelNode {
     int status, n_inner, n_outer, conv_out, bad, done;
 };
 
-// 1/2 (1 - psi) D and 1/2 (3 psi - 1) D / |I|^2 of K_jk = a delta_jk + c I_j I_k
-// (Eq. eddingtonTensor with Minerbo's psi, Eq. eddingtonFactorMinerbo): the flux
-// factor h = |I| / D is clipped to [0, 1], and c = 0 where |I| = 0 (psi(0) = 1/3).
+// a = 1/2 (1 - psi) D and c = 1/2 (3 psi - 1) D / |I|^2 of K_jk = a delta_jk + c I_j I_k
+// (Eq. eddingtonTensor with Minerbo's psi, Eq. eddingtonFactorMinerbo), h = |I| / D
+// clipped to [0, 1].  With Minerbo's polynomial, 3 psi - 1 = (2/5)(3 - h + 3h^2) h^2,
+// so for h < 1, c = (3 - h + 3h^2) / (5 D): no division by |I|^2 and no cancellation in
+// 3 psi - 1 (whose FP64 rounding residue over a |I|^2 decayed into the denormals would
+// overflow).  At h = 1 (|I| >= D > 0) psi = 1 and c = D / |I|^2.  D <= 0: K = (D/3) delta.
 __device__ __forceinline__ void closure_ac(double D, double I0, double I1, double I2, double& a, double& c) {
     const double In2 = I0 * I0 + I1 * I1 + I2 * I2;
-    const double In = sqrt(In2);
-    double h = D > 0.0 ? In / D : 0.0;
-    h = fmin(fmax(h, 0.0), 1.0);
-    const double psi = 1.0 / 3.0 + (2.0 / 15.0) * (3.0 - h + 3.0 * h * h) * h * h;
-    a = 0.5 * (1.0 - psi) * D;
-    c = In2 > 0.0 ? 0.5 * (3.0 * psi - 1.0) * D / In2 : 0.0;
+    if (!(D > 0.0)) {
+        a = D / 3.0;
+        c = 0.0;
+        return;
+    }
+    const double h = sqrt(In2) / D;
+    if (h >= 1.0) {
+        a = 0.0;
+        c = D / In2;
+        return;
+    }
+    const double p = 3.0 - h + 3.0 * h * h;
+    a = 0.5 * (2.0 / 3.0 - (2.0 / 15.0) * p * h * h) * D;   // 1 - psi = 2/3 - (2/15) p h^2
+    c = p / (5.0 * D);
 }
 
 // The fifteen per-thread terms of the Eulerian sums at moments (D, I).
