@@ -52,7 +52,7 @@ WORKLOAD = ("collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, EmAb
 # the kernel has changed since its counters were taken.
 TRAFFIC_PER_NODE = {"fused_kernel<double>": 521435392 / 65536, "fused_kernel<float>": 510243328 / 65536,
                     "adjoint_kernel": 875135232 / 65536, "velocity_kernel": 525478656 / 65536,
-                    "c2p_kernel": None}
+                    "c2p_kernel": 530723584 / 65536}
 
 
 def _traffic(kernel, n):
