@@ -294,13 +294,14 @@ int collision_solve_noalloc(nmc_ctx* ctx, const nmc_params* params, int64_t n,
  * per variant of the fused kernel that fits the shape: register class
  * (__launch_bounds__ blocks per SM: 3..6 at 128 threads, 1..3 at 256) times a
  * persistent grid of 100% or 50% of the resident capacity.  Each variant runs
- * once untimed and once between CUDA events on `stream` (the call
- * synchronises it).  The fastest is kept in the context for this precision,
+ * twice, each run between CUDA events on `stream` (the call synchronises it),
+ * and its faster run counts.  The fastest is kept in the context for this precision,
  * Anderson depth (m_inner <= 3 or <= 5) and block class, and later
  * collision_solve calls with matching parameters use it; untuned keys use 4
  * (128 threads), 2 (256) or 1 (512) blocks per SM and the full grid.
- * Arguments as collision_solve (the outputs hold the last variant's results,
- * identical for every variant); chosen[2] receives (blocks per SM, grid %)
+ * Arguments as collision_solve (the outputs hold the last variant's results;
+ * variants are separate compilations and agree to the solve's accuracy);
+ * chosen[2] receives (blocks per SM, grid %)
  * and *ms the winner's time (either may be NULL).  n in 1..2^30.
  */
 int nmc_autotune(nmc_ctx* ctx, const nmc_params* params, int64_t n,
