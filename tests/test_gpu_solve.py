@@ -161,7 +161,7 @@ def test_full_size_profile_sampled_and_conservation():
     ref = _oracle(g, tables, inp, nodes, **TIGHT)
     for n, r in zip(nodes, ref):
         compare_node(out, n, r, g.W2, PARITY)
-    # BASELINE tolerance: still conservative to 1e-12 and close to the tight answer
+    # at the default tolerance (1e-10): still conservative to 1e-12 and close to the tight answer
     out2 = gpu_solve(ctx, inp)
     assert np.all(out2["status"] == 0)
     dl, de = _conservation(g, inp["rho"], inp["Ye"], eps0, inp["D"], out2["Ye"], out2["eps"], out2["J"])
