@@ -30,6 +30,10 @@ Readings of points the paper leaves open (each also listed in the design notes):
 * an outer iterate outside the EoS domain (Ye not in (0, 1), or eps outside
   the range of the EoS at that Ye) sets EOS_FAIL and stops the outer loop; the
   returned temperature is then the last one inside the domain;
+* semi_implicit=True skips ComputeOpacities after the first outer iteration,
+  so every opacity (chi_EmAb, sigma_Iso, D^Eq and the NES and pair kernels)
+  stays at the old state y* (the semi-implicit variant of Sec. 3.5); the outer
+  loop still iterates y, whose temperature is then used only for the output;
 * after outer convergence the returned matter state is q(M, y) evaluated at
   the converged moments, so lepton number and energy are conserved to
   rounding (final_q=True); final_q=False returns the Anderson-mixed iterate
@@ -56,7 +60,7 @@ class Params:
     def __init__(self, tol_inner=1e-10, tol_outer=1e-10, M_inner=3, M_outer=3,
                  max_inner=500, max_outer=100, dmin=1e-30, dmax=1.0 - 1e-6,
                  norm_floor=1e-30, proc_mask=ALL_PROCESSES, frozen_matter=False,
-                 final_q=True):
+                 final_q=True, semi_implicit=False):
         self.tol_inner = tol_inner
         self.tol_outer = tol_outer
         self.M_inner = M_inner
@@ -69,6 +73,7 @@ class Params:
         self.proc_mask = proc_mask
         self.frozen_matter = frozen_matter
         self.final_q = final_q
+        self.semi_implicit = semi_implicit
 
 
 def compute_rates(D, op, W2):
@@ -185,7 +190,7 @@ def solve_node(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, s
     outer_converged = False
     while not outer_converged:
         k += 1
-        if k > 1:
+        if k > 1 and not p.semi_implicit:
             op = compute_opacities(grid, tables, rho, T, y[1], scale, p.proc_mask, p.dmin, p.dmax)
             if op["clamped"]:
                 status |= TABLE_CLAMP

@@ -207,7 +207,7 @@ def solve_node(grid, tables, params, rho, T_star, Ye_star, v_star, D_star, I_sta
     outer_converged = False
     while not outer_converged:
         k += 1
-        if k > 1:
+        if k > 1 and not p.semi_implicit:   # semi-implicit: opacities at y* only
             op = compute_opacities(grid, tables, rho, T, y[4], scale, p.proc_mask, p.dmin, p.dmax)
             if op["clamped"]:
                 status |= TABLE_CLAMP

@@ -105,14 +105,16 @@ def test_no_exchange_without_time_step(grid_tiny):
     assert r["T"] == pytest.approx(a["T"], rel=1e-12)
 
 
-def unrelaxed_residuals(grid, t, a, v_star, r):
+def unrelaxed_residuals(grid, t, a, v_star, r, at=None):
     """Residuals of Eqs. implicitNumberNodal and implicitNumberFluxNodal at the returned state,
     relative to the size of their terms: (D + v.I) - N* - dtau (eta - chi D) and
-    (I_j + v^i K_ij) - G*_j + dtau kappa I_j, with the opacities at the returned matter state."""
+    (I_j + v^i K_ij) - G*_j + dtau kappa I_j, with the opacities at the matter state `at` = (T, Ye),
+    by default the returned one."""
     W2 = grid.W2
     dtau = C_LIGHT * a["dt"]
     D, I, v = r["D"], r["I"], r["v"]
-    op = compute_opacities(grid, t, a["rho"], r["T"], r["Ye"], a["scale"], solver.ALL_PROCESSES, 1e-30, 1 - 1e-6)
+    T_op, Ye_op = (r["T"], r["Ye"]) if at is None else at
+    op = compute_opacities(grid, t, a["rho"], T_op, Ye_op, a["scale"], solver.ALL_PROCESSES, 1e-30, 1 - 1e-6)
     en, cn, ep, cp = solver.compute_rates(D, op, W2)
     eta = op["chi_ab"] * op["deq"] + en + ep
     chi = op["chi_ab"] + cn + cp
