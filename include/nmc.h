@@ -147,13 +147,18 @@ typedef struct {
     int32_t frozen_matter; /* 1: y fixed at y*, single outer iteration */
     int32_t final_q;       /* 1: return y = q(M, y) at the converged moments (exact
                               conservation); 0: the Anderson-mixed iterate of Alg. 1 */
-    int32_t reserved;
+    int32_t semi_implicit; /* 1: ComputeOpacities once, at the old state y* before
+                              the outer loop of Algorithm 1, and not after matter
+                              updates: the semi-implicit variant of Sec. 3.5;
+                              0: fully implicit.
+                              collision_solve and collision_solve_v; collision_adjoint
+                              returns NMC_EUNSUPPORTED for it */
     double  d_min, d_max;  /* bounds of the D^Eq limiter (Eq. fermiDiracProjection) */
     double  norm_floor;    /* Algorithm 2 reference norm floored at norm_floor*sqrt(sum W2) */
 } nmc_params;
 
 /* Fills defaults: tol 1e-10, M = 3, caps 100, FP64, fused, all processes,
- * d_min 1e-30, d_max 1 - 1e-6, norm_floor 1e-30, final_q 1. */
+ * d_min 1e-30, d_max 1 - 1e-6, norm_floor 1e-30, final_q 1, semi_implicit 0. */
 void nmc_default_params(nmc_params* p);
 
 /*

@@ -131,6 +131,7 @@ void nmc_default_params(nmc_params* p) {
     p->proc_mask = NMC_PROC_ALL;
     p->frozen_matter = 0;
     p->final_q = 1;
+    p->semi_implicit = 0;
     p->d_min = 1e-30;
     p->d_max = 1.0 - 1e-6;
     p->norm_floor = 1e-30;
@@ -370,6 +371,7 @@ int nmc_check_params_internal(nmc_ctx* ctx, const nmc_params* p) {
     if (!(p->d_min > 0.0) || !(p->d_max < 1.0) || !(p->d_min < p->d_max))
         return set_error(ctx, NMC_EINVAL, "need 0 < d_min < d_max < 1");
     if (!(p->norm_floor >= 0.0)) return set_error(ctx, NMC_EINVAL, "norm_floor must be >= 0");
+    if (p->semi_implicit != 0 && p->semi_implicit != 1) return set_error(ctx, NMC_EINVAL, "semi_implicit must be 0 or 1");
     return NMC_OK;
 }
 
@@ -496,6 +498,8 @@ int collision_adjoint(nmc_ctx* ctx, const nmc_params* params, int64_t n, const d
     if (!ctx) return NMC_EINVAL;
     int rc = nmc_check_params_internal(ctx, params);
     if (rc != NMC_OK) return rc;
+    if (params->semi_implicit)
+        return set_error(ctx, NMC_EUNSUPPORTED, "collision_adjoint differentiates the fully implicit solve only");
     if (n < 0) return set_error(ctx, NMC_EINVAL, "n < 0");
     if (n == 0) return NMC_OK;
     if (!rho || !T_in || !Ye_in || !J_in || !dt || !J_out || !gJ_in || !gYe_in || !gT_in)

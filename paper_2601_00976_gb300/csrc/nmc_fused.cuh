@@ -216,8 +216,11 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
 
         for (int k = 1;; ++k) {
             // ================= ComputeOpacities(y^[k]) =================
-            compute_opacities<R>(g, a.tb, P, nd->rho, nd->T, nd->y[1], nd->dtau, nd->sc, ob, &nd->op,
-                                 &nd->status, chiab, sig, deq, deqc, lead);
+            // semi-implicit (Sec. 3.5): only at y^[1] = y*; the shared kernels, chiab, sig and
+            // D^Eq of the first outer iteration stay in place (nothing else writes them)
+            if (k == 1 || !P.semi_implicit)
+                compute_opacities<R>(g, a.tb, P, nd->rho, nd->T, nd->y[1], nd->dtau, nd->sc, ob, &nd->op,
+                                     &nd->status, chiab, sig, deq, deqc, lead);
             if constexpr (kMixed) {
                 const double c1 = (double)Wt, c2 = c1 * (double)chiab;
                 A0x = f2_from(c1 * Dsd + c2 * (double)deq);

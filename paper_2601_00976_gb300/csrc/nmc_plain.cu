@@ -72,6 +72,7 @@ struct PlainShared {
     double alpha[kPlainMaxM];
     OpacState op;
     int status, conv, bad, slot;
+    int reuse;   // semi-implicit, outer iteration > 1: the node's opacities in global memory stand
 };
 
 __device__ __forceinline__ int append(int* list, int* count, int slot) {
@@ -166,30 +167,36 @@ __global__ void __launch_bounds__(512) plain_opacity_kernel(const SolveArgs a, P
             sh->Ye = nd->y[1];
             for (int k = 0; k < 4; ++k) sh->sc[k] = nd->sc[k];
             sh->status = nd->status;
+            // semi-implicit (Sec. 3.5): ComputeOpacities only at y^[1] = y*; the slot's kernel
+            // matrices and per-energy opacities from the first outer iteration are kept
+            sh->reuse = P.semi_implicit && nd->k > 0;
         }
         __syncthreads();
-        double chiab = 0.0, sig = 0.0, deq = 0.0, deqc = 0.0;
-        compute_opacities<double>(g, a.tb, P, sh->rho, sh->T, sh->Ye, sh->dtau, sh->sc, ob, &sh->op, &sh->status,
-                                  chiab, sig, deq, deqc);
-        // kernel matrices and per-energy opacities to global memory
-        const long long mat = (long long)NE * NE;
-        for (int sp = 0; sp < NS; ++sp) {
-            double* dst = st.kout + ((long long)slot * NS + sp) * mat;
-            for (int i = tid; i < NE * NE; i += blockDim.x) dst[i] = phi[sp * NE * LD + (i / NE) * LD + i % NE];
-        }
-        for (int pr = 0; pr < NS / 2; ++pr) {
-            double* dst = st.kann + ((long long)slot * (NS / 2) + pr) * mat;
-            for (int i = tid; i < NE * NE; i += blockDim.x) dst[i] = ann[pr * NE * LD + (i / NE) * LD + i % NE];
+        const bool reuse = sh->reuse != 0;
+        if (!reuse) {
+            double chiab = 0.0, sig = 0.0, deq = 0.0, deqc = 0.0;
+            compute_opacities<double>(g, a.tb, P, sh->rho, sh->T, sh->Ye, sh->dtau, sh->sc, ob, &sh->op,
+                                      &sh->status, chiab, sig, deq, deqc);
+            // kernel matrices and per-energy opacities to global memory
+            const long long mat = (long long)NE * NE;
+            for (int sp = 0; sp < NS; ++sp) {
+                double* dst = st.kout + ((long long)slot * NS + sp) * mat;
+                for (int i = tid; i < NE * NE; i += blockDim.x) dst[i] = phi[sp * NE * LD + (i / NE) * LD + i % NE];
+            }
+            for (int pr = 0; pr < NS / 2; ++pr) {
+                double* dst = st.kann + ((long long)slot * (NS / 2) + pr) * mat;
+                for (int i = tid; i < NE * NE; i += blockDim.x) dst[i] = ann[pr * NE * LD + (i / NE) * LD + i % NE];
+            }
+            if (act) {
+                const long long o = ((long long)slot * NS + s) * NE + q;
+                st.chiab[o] = chiab;
+                st.sig[o] = sig;
+                st.deq[o] = deq;
+                st.va[o] = vA[sq];
+            }
         }
         double M0 = 0.0;
-        if (act) {
-            const long long o = ((long long)slot * NS + s) * NE + q;
-            st.chiab[o] = chiab;
-            st.sig[o] = sig;
-            st.deq[o] = deq;
-            st.va[o] = vA[sq];
-            M0 = a.J_out[(n * NS + s) * NE + q];
-        }
+        if (act) M0 = a.J_out[(n * NS + s) * NE + q];
         {   // reference norm ||D^[k,1]||_W per species (Algorithm 2 input)
             double v[1] = {Wt * M0 * M0};
             species_sum<1, double>(v, red, sh->sp_out, NEP, NS);

@@ -295,11 +295,14 @@ __global__ void __launch_bounds__(MAXT, MINB) velocity_kernel(const VelArgs va) 
         }
         double M[4] = {Ds, Is[0], Is[1], Is[2]};
         int outer_exit = 0;
+        double chiab = 0, sig = 0, deq = 0, deqc = 0;
 
         for (int k = 1;; ++k) {
-            double chiab = 0, sig = 0, deq = 0, deqc = 0;
-            compute_opacities<double>(g, a.tb, P, nd->rho, nd->T, nd->y[4], nd->dtau, nd->sc, ob, &nd->op,
-                                      &nd->status, chiab, sig, deq, deqc, lead);
+            // semi-implicit (Sec. 3.5): ComputeOpacities only at y^[1] = y*; its shared kernels
+            // and this thread's chiab, sig and D^Eq stay in place for the later outer iterations
+            if (k == 1 || !P.semi_implicit)
+                compute_opacities<double>(g, a.tb, P, nd->rho, nd->T, nd->y[4], nd->dtau, nd->sc, ob, &nd->op,
+                                          &nd->status, chiab, sig, deq, deqc, lead);
             const double vk[3] = {nd->y[0], nd->y[1], nd->y[2]};
             const double lam = nd->lam;
             {   // reference norm ||D^[k,1]||_W per species and the Algorithm 2 thresholds

@@ -51,7 +51,7 @@ class Params(ctypes.Structure):
                 ("max_inner", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("proc_mask", ctypes.c_int32), ("frozen_matter", ctypes.c_int32),
-                ("final_q", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("final_q", ctypes.c_int32), ("semi_implicit", ctypes.c_int32),
                 ("d_min", ctypes.c_double), ("d_max", ctypes.c_double),
                 ("norm_floor", ctypes.c_double)]
 
