@@ -51,8 +51,8 @@ WORKLOAD = ("collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, EmAb
 # DRAM bytes (read + write) per node of one launch, from ncu captures of the 2^16-node profile
 # (dram__bytes_read.sum + dram__bytes_write.sum); traffic grows with the node count.  None where
 # the kernel has changed since its counters were taken.
-TRAFFIC_PER_NODE = {"fused_kernel<double>": 521435392 / 65536, "fused_kernel<float>": 510243328 / 65536,
-                    "adjoint_kernel": 875135232 / 65536, "velocity_kernel": 525478656 / 65536,
+TRAFFIC_PER_NODE = {"fused_kernel<double>": 516098560 / 65536, "fused_kernel<float>": 505901312 / 65536,
+                    "adjoint_kernel": 875135232 / 65536, "velocity_kernel": 524328704 / 65536,
                     "c2p_kernel": 530723584 / 65536}
 
 
