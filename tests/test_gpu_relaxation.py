@@ -7,6 +7,8 @@ dt from 1e-4 ms growing by 1.04 per step to t = 100 ms (271 steps).
 
 * The first steps follow the oracle's backward-Euler trajectory (oracle/velocity.py step by step)
   to 1e-9 at tol 1e-12 on both sides.
+* Both tests run fully implicit and semi-implicit (opacities at each step's old state, Sec. 3.5);
+  every step conserves in either, and both relax to the same equilibrium.
 * Over the whole run every step converges; total lepton number and total energy are conserved
   to 1e-10 relative (each step conserves them to rounding).
 * At t = 100 ms every species has relaxed to the local equilibrium from a distribution far from
@@ -30,23 +32,26 @@ V0 = (0.1, 0.0, 0.0)
 NS = 6
 
 
-def _setup(tol):
+def _setup(tol, semi=0):
     edges, _ = ogrid.geometric_edges(16, 1.875)
     g = ogrid.EnergyGrid(edges, 2)
     tables = synthetic.make_tables(g.eps, NS, seed=81)
     ctx = nmc.Context(edges, 2, NS, tables)
     D0, I0 = relaxation.initial_moments(ctx.energies, NS, T0)
     dev = dict(dtype=torch.float64, device="cuda")
-    p = nmc.default_params(tol_inner=tol, tol_outer=tol, m_inner=2, m_outer=2, max_inner=1000, max_outer=200)
+    p = nmc.default_params(tol_inner=tol, tol_outer=tol, m_inner=2, m_outer=2, max_inner=1000, max_outer=200,
+                           semi_implicit=semi)
     rel = relaxation.Relaxation(ctx, p, torch.tensor([RHO], **dev), torch.tensor([T0], **dev),
                                 torch.tensor([YE0], **dev), torch.tensor([V0], **dev),
                                 torch.tensor(D0[None], **dev), torch.tensor(I0[None], **dev))
     return g, tables, ctx, rel, D0, I0
 
 
-def test_first_steps_follow_the_oracle():
-    g, tables, ctx, rel, D0, I0 = _setup(1e-12)
-    P = osolver.Params(tol_inner=1e-12, tol_outer=1e-12, M_inner=2, M_outer=2, max_inner=2000, max_outer=300)
+@pytest.mark.parametrize("semi", [0, 1])
+def test_first_steps_follow_the_oracle(semi):
+    g, tables, ctx, rel, D0, I0 = _setup(1e-12, semi)
+    P = osolver.Params(tol_inner=1e-12, tol_outer=1e-12, M_inner=2, M_outer=2, max_inner=2000, max_outer=300,
+                       semi_implicit=bool(semi))
     D, I, T, Ye, v = D0, I0, T0, YE0, np.array(V0)
     for dt in relaxation.schedule()[:6]:
         r = ovel.solve_node(g, tables, P, RHO, T, Ye, v, D, I, dt)
@@ -63,8 +68,9 @@ def test_first_steps_follow_the_oracle():
         D, I, T, Ye, v = r["D"], r["I"], r["T"], r["Ye"], r["v"]
 
 
-def test_relaxation_run_conserves_and_reaches_equilibrium():
-    g, tables, ctx, rel, D0, I0 = _setup(1e-8)
+@pytest.mark.parametrize("semi", [0, 1])
+def test_relaxation_run_conserves_and_reaches_equilibrium(semi):
+    g, tables, ctx, rel, D0, I0 = _setup(1e-8, semi)
     L0, E0 = (x.item() for x in rel.totals())
     outer, inner = [], []
 
