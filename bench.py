@@ -53,7 +53,7 @@ WORKLOAD = ("collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, EmAb
 # the kernel has changed since its counters were taken.
 TRAFFIC_PER_NODE = {"fused_kernel<double>": 516098560 / 65536, "fused_kernel<float>": 505901312 / 65536,
                     "adjoint_kernel": 875135232 / 65536, "velocity_kernel": 524328704 / 65536,
-                    "c2p_kernel": 530723584 / 65536}
+                    "c2p_kernel": 530723584 / 65536, "opacity_interp_kernel": None}
 
 
 def _traffic(kernel, n):
@@ -71,6 +71,10 @@ C2P_WORKLOAD = ("conserved-to-primitive recovery of every bin (collapse profile,
                 "energies, conserved moments of the profile's occupations, infall velocity up to 0.15 c), FP64, "
                 "tol 1e-8, Anderson memory 3")
 C2P_BYTES_PER_BIN = 68    # N, G in; D, I, iteration count out (8 + 24 + 8 + 24 + 4 bytes)
+INTERP_WORKLOAD = ("opacity_interp: chi_EmAb and sigma_Iso of each of 4 species (8 launches per step) at 2^23 "
+                   "scattered points, (rho, T, Ye) uniform in (log10 rho, log10 T, Ye) over the tables and E "
+                   "log-uniform over Grid C 16x2's node energies, FP64, inputs larger than L2")
+INTERP_BYTES_PER_POINT = 40   # rho, T, Ye, E in and the interpolated value out, f64, per launch
 VEL_WORKLOAD = ("O(v/c) solve (collapse profile, 2^16 nodes, 4 species, Grid C 16x2 energies, all processes, "
                 "infall velocity field up to 0.15 c, Minerbo closure, FP64, tol 1e-10, Anderson depth 3)")
 ADJ_WORKLOAD = ("gradient of the FP64 solve (collapse profile, 2^18 nodes, 4 species, Grid C 16x2 energies, "
@@ -92,6 +96,8 @@ def _args():
                     help="nodes of the O(v/c) solve measurement (0 skips it)")
     ap.add_argument("--c2p-nodes", type=int, default=N_NODES,
                     help="nodes of the conserved-to-primitive measurement (0 skips it)")
+    ap.add_argument("--interp-points", type=int, default=1 << 23,
+                    help="points of the opacity_interp measurement (0 skips it)")
     ap.add_argument("--relaxation-problems", type=int, default=4096,
                     help="problems in the relaxation-driver measurement (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -276,6 +282,18 @@ def cpu_baseline(edges, tables, inp):
 
 
 FP32_PEAK_TFLOPS = 80.6   # dense FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (recipe unit count and clock)
+
+
+def _measured_hbm_gbs():
+    """Measured copy bandwidth of this GPU model (MEASURED_PEAKS.json beside this file), else 6800 GB/s."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _measured_hbm_gbs()
 # inner, outer tolerances of the mixed path: where dtau chi ~ 1e4 the heavy flavours' number-conserving
 # mode keeps an error ~ tol (1 + dtau chi), so the stated <= 1e-5 error needs tol ~ 1e-9 (measured max
 # D error against the FP64 path on this workload: 4.6e-7; at 1e-6 it is 1.1e-3)
@@ -458,6 +476,49 @@ def time_c2p(args, ctx, eps, dev, rank, barrier, allmax, stream):
                          "algorithmic_flops_per_launch": fl, "kernel_ms": kern_ms}}
 
 
+def time_interp(args, ctx, eps, dev, rank, barrier, allmax, stream):
+    """Time opacity_interp (FP64): chi_EmAb and sigma_Iso of every species at scattered points."""
+    import torch
+    from paper_2601_00976_gb300 import synthetic, flops
+    from paper_2601_00976_gb300.dist import workload_seed, weak_scaling_value
+    P = args.interp_points
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    pts = {k: torch.tensor(v, device=dev) for k, v in synthetic.make_interp_points(P, eps, seed=workload_seed(rank, 5)).items()}
+    outs = [torch.empty(P, dtype=torch.float64, device=dev) for _ in range(2 * NS)]
+    launches = [(which, sp) for which in (0, 1) for sp in range(NS)]
+
+    def step():
+        for k, (which, sp) in enumerate(launches):
+            ctx.opacity_interp(which, sp, pts["rho"], pts["T"], pts["Ye"], pts["E"], out=outs[k])
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    barrier()
+    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evs) / len(launches)
+    total_ms = allmax(evs[0][0].elapsed_time(evs[-1][1]))
+    finite = all(bool(torch.isfinite(o).all().item()) and bool((o > 0).all().item()) for o in outs)
+    fl = flops.interp_point_flops() * P
+    ach = fl / (launch_ms * 1e-3) / 1e12
+    gbs = INTERP_BYTES_PER_POINT * P / (launch_ms * 1e-3) / 1e9
+    return {"metric": "interpolated opacities/s (points*launches*steps/s)",
+            "value": weak_scaling_value(ws * P * len(launches), args.steps, total_ms), "unit": "points/s",
+            "ms_per_step": total_ms / args.steps, "dtype": "f64",
+            "config": {"workload": INTERP_WORKLOAD, "points_per_gpu": P, "launches_per_step": len(launches),
+                       "all_values_finite_positive": finite,
+                       "hbm_gbs_algorithmic": gbs, "hbm_frac_of_measured": gbs / HBM_PEAK_GBS},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach / FP64_PEAK_TFLOPS, "traffic": _traffic("opacity_interp_kernel", P),
+                         "kernel": "opacity_interp_kernel",
+                         "peak_source": "derived FP64 FMA rate at 2.07 GHz; exp and log count 1 flop",
+                         "algorithmic_flops_per_launch": fl, "kernel_ms": launch_ms}}
+
+
 def time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream):
     """Time collision_adjoint over the adjoint workload (inputs and cotangents resident in HBM)."""
     import torch
@@ -629,6 +690,7 @@ def run_nmc(args):
 
     vel = time_velocity(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.velocity_nodes > 0 else None
     c2p = time_c2p(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.c2p_nodes > 0 else None
+    itp = time_interp(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.interp_points > 0 else None
     rlx = time_relaxation(args, dev, rank, barrier, allmax) if args.relaxation_problems > 0 else None
     adj = time_adjoint(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.adjoint_nodes > 0 else None
     bat = time_batching(args, ctx, eps, dev, rank, barrier, allmax, stream) if args.batching_nodes > 0 else None
@@ -679,6 +741,8 @@ def run_nmc(args):
             line["velocity"] = vel
         if c2p is not None:
             line["c2p"] = c2p
+        if itp is not None:
+            line["opacity_interp"] = itp
         if rlx is not None:
             line["relaxation"] = rlx
         if adj is not None:

@@ -89,3 +89,18 @@ def c2p_bin_flops(iters):
     once: lambda and the reference norm                              -> 10
     """
     return 120 * iters + 10
+
+
+def interp_point_flops():
+    """Algorithmic flops of one opacity_interp point (tetralinear in log10 rho, log10 T, Ye, ln E).
+
+    two log10 and one ln of the coordinates                   -> 3
+    cell offsets and fractions on four axes (2 each, the
+    energy fraction a division more)                          -> 9
+    the complements 1 - t of three axes                       -> 3
+    per corner of the (rho, T, Ye) cube: its weight (2),
+    the linear blend of the two energy entries (3), the
+    weighted accumulation (FMA, 2)                            -> 8 x 7
+    exp of the interpolated logarithm                         -> 1
+    """
+    return 3 + 9 + 3 + 8 * 7 + 1

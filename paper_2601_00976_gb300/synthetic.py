@@ -222,3 +222,18 @@ def make_velocities(kind, N, seed=0, vmax=0.15):
     v[:, 0] = -2.0 * vmax * x / (1.0 + x * x)
     v[:, 1:] = 0.01 * vmax * rng.normal(size=(N, 2))
     return v
+
+
+def make_interp_points(P, energies, seed=0):
+    """Scattered matter states and energies for opacity_interp; data only.
+
+    (rho, T, Ye) uniform in (log10 rho, log10 T, Ye) over the table axes and E
+    log-uniform between the lowest and highest node energy, so every lookup is
+    an interior, tetralinear one at an unrelated table cell.
+    """
+    rng = np.random.default_rng(seed + 104729)
+    e = np.asarray(energies, dtype=float)
+    return dict(rho=10.0 ** rng.uniform(RHO_AXIS[0], RHO_AXIS[1], size=P),
+                T=10.0 ** rng.uniform(T_AXIS[0], T_AXIS[1], size=P),
+                Ye=rng.uniform(YE_AXIS[0], YE_AXIS[1], size=P),
+                E=np.exp(rng.uniform(math.log(e[0]), math.log(e[-1]), size=P)))
