@@ -95,3 +95,31 @@ def test_grid_nodes_helper(lib):
         assert np.allclose(eps, g.eps, rtol=1e-15)
         assert np.allclose(w2, g.W2, rtol=1e-13)
         assert np.allclose(w3, g.W3, rtol=1e-13)
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of nmc_grid, nmc_tables and nmc_params have the header's
+    field offsets and sizes (compiled with the host C compiler)."""
+    import shutil
+    import subprocess
+    from paper_2601_00976_gb300 import nmc
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"nmc_grid": nmc.Grid, "nmc_tables": nmc.Tables, "nmc_params": nmc.Params}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nmc.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'    printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c = {(a, b): int(v) for a, b, v in (ln.split() for ln in out if ln)}
+    for cname, py in structs.items():
+        assert c[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert c[(cname, field)] == getattr(py, field).offset, (cname, field)
