@@ -175,8 +175,26 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tables, nmc_ctx** out);
 /* Releases every device and host allocation of the context; NULL is a no-op. */
 void nmc_destroy(nmc_ctx* ctx);
 
-/* Message for the last failed call on ctx (static string if ctx is NULL). */
+/* Message for the last failed call on ctx (static string if ctx is NULL).
+ * In an NMC_DEBUG build it first reads the context's bounds-check error word
+ * (a device copy, which waits for the device) and, if a check failed, names
+ * its site. */
 const char* nmc_last_error(const nmc_ctx* ctx);
+
+/*
+ * Bounds checks of the NMC_DEBUG build (a debugging aid; the paper has no
+ * counterpart).  The library built with -DNMC_DEBUG checks every table,
+ * shared-memory, least-squares-history and output index of the collision
+ * solve's kernels against the length of the array it addresses; a failed
+ * check records its site (1 EmAb/Iso table, 2 NES table, 3 pair table,
+ * 4 shared NES matrix, 5 shared pair matrix, 6 shared vectors, 7 shared
+ * Fermi--Dirac values, 8 least-squares history, 9 output, 10 projection
+ * operators) in a device word of the context, skips the access, and the
+ * persistent kernels stop taking nodes; nothing traps.  This call copies the
+ * word to *word (0: no check failed), clearing it when `clear` is nonzero; it
+ * waits for the device.  The release build returns NMC_EUNSUPPORTED.
+ */
+int nmc_debug_word(nmc_ctx* ctx, uint32_t* word, int32_t clear);
 
 /* Writes the node energies eps_q (MeV), W2_q (cm^-3) and W3_q (MeV cm^-3) of
  * the context's grid into HOST arrays of length ne (any may be NULL). */
@@ -279,8 +297,15 @@ int conserved_to_primitive(nmc_ctx* ctx, int64_t n, const double* N_in, const do
  * routine.  Limits and behaviour:
  * - n <= 2^30 per call (the counter is 32-bit); larger n returns
  *   NMC_EUNSUPPORTED with a message.
- * - The first call on a device looks up the array's device address with that
- *   device current; make that first call before any stream capture.
+ * - Set-up is done by nmc_create, which may allocate: it looks up the array's
+ *   device address for the context's device (with that device current) and
+ *   loads the fused kernel's variants, which CUDA's lazy module loading would
+ *   otherwise load, reserving memory, at their first launch.  The driver can
+ *   still size its local-memory reservation for the kernel at the kernel's
+ *   first launch on the context, so make one call (a warm-up) during set-up,
+ *   before the phase in which nothing may allocate and before any stream
+ *   capture; later calls leave the device's free memory unchanged.
+ * - The context's device must be the current device (NMC_EINVAL otherwise).
  * - Every call on a device shares the array, and each call clears the counter
  *   on its stream before the kernel starts: calls that overlap on the GPU
  *   (different streams, or concurrent host threads) race and must not be
@@ -293,6 +318,31 @@ int collision_solve_noalloc(nmc_ctx* ctx, const nmc_params* params, int64_t n,
                             double* J_out, double* H_out, double* Ye_out, double* eps_out,
                             double* T_out, int32_t* n_outer, int32_t* n_inner, uint32_t* status,
                             void* stream);
+
+/*
+ * collision_solve on HOST buffers (the paper has no counterpart: this is the
+ * call for a caller whose node data live in host memory).  Same arguments,
+ * parameters and results as collision_solve, except that every array is a
+ * HOST pointer (page-locked memory lets the copies overlap the solve; pageable
+ * memory works but serialises them) and `chunk` sets the pipeline's chunk
+ * size in nodes (0: n / 8, at least 8192).  The batch is copied to the device
+ * chunk by chunk on an upload stream, each chunk is solved on `stream`, and
+ * its outputs are copied back on a download stream, so that copies of
+ * neighbouring chunks overlap the solve; `stream` waits for the last copies,
+ * so the host outputs are complete once `stream` is (synchronise it before
+ * reading them; keep the host buffers alive until then).  The context keeps
+ * device staging for two chunks (allocated on the first call that needs it,
+ * freed by nmc_destroy) and two streams of its own; calls on one context must
+ * not overlap.  n <= 2^30; NMC_EINVAL for NULL arrays (opac_scale may be
+ * NULL), NMC_ENOMEM when the staging cannot be allocated.
+ */
+int collision_solve_host(nmc_ctx* ctx, const nmc_params* params, int64_t n,
+                         const double* rho, const double* T_in, const double* Ye_in,
+                         const double* J_in, const double* H_in, const double* dt,
+                         const double* opac_scale,
+                         double* J_out, double* H_out, double* Ye_out, double* eps_out,
+                         double* T_out, int32_t* n_outer, int32_t* n_inner, uint32_t* status,
+                         int64_t chunk, void* stream);
 
 /*
  * Autotuner of the fused mode.  Runs collision_solve on the given batch once
@@ -336,6 +386,19 @@ int nmc_set_plain_chunk(nmc_ctx* ctx, int64_t nodes);
 int opacity_interp(nmc_ctx* ctx, int32_t which, int32_t species, int64_t p,
                    const double* rho, const double* T, const double* Ye, const double* E,
                    double* out, void* stream);
+
+/*
+ * The same interpolation (Sec. 2.3) in FP32: the mixed-precision solve's FP32
+ * copies of the ln tables, FP32 logarithms of the coordinates, cell search,
+ * weights and blend (the ln value as its first corner plus weighted
+ * differences), and an FP32 exp.  Arguments, clamping and errors as
+ * opacity_interp (DEVICE float64 in and out); values agree with the FP64
+ * entry point to ~1e-6 relative (FP32 rounding of the ln tables and of the
+ * coordinates' logarithms), for callers that run the mixed path.
+ */
+int opacity_interp_mixed(nmc_ctx* ctx, int32_t which, int32_t species, int64_t p,
+                         const double* rho, const double* T, const double* Ye, const double* E,
+                         double* out, void* stream);
 
 /*
  * Gradient of a converged collision_solve at n nodes (FP64), by the
@@ -391,6 +454,22 @@ int collision_adjoint(nmc_ctx* ctx, const nmc_params* params, int64_t n,
                       const double* geps_out, const double* gT_out,
                       double* gJ_in, double* gH_in, double* gYe_in, double* gT_in,
                       double* gscale, uint32_t* status, void* stream);
+
+/*
+ * FMA-pipe peak probe (a measurement helper; the paper has no counterpart).
+ * The collision solve is per-node dense arithmetic, so its roofline is the
+ * FMA pipe of its precision, not HBM: FP64 for NMC_FP64, FP32 for NMC_MIXED.
+ * Launches, on `stream`, one kernel in which every thread of a full-occupancy
+ * grid (blocks_per_sm <= 0: as many 512-thread blocks per SM as fit; else
+ * that many) advances sixteen independent FMA chains for `iters` steps, and
+ * stores in *flops the launch's flop count (2 per FMA).  The caller times the
+ * launch with CUDA events on `stream`.  sink: DEVICE buffer of one element of
+ * the precision's type, written only to keep the work live (its value is
+ * meaningless).  NMC_EINVAL for iters < 1, a NULL sink or another precision;
+ * NMC_ECUDA for a failed launch.
+ */
+int nmc_fma_probe(int32_t precision, int32_t blocks_per_sm, int32_t iters, void* sink, double* flops,
+                  void* stream);
 
 #ifdef __cplusplus
 }

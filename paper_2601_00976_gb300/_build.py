@@ -15,6 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libnmc.so")
+# the NMC_DEBUG build (bounds checks that record a failed index in a device error word)
+OUT_DEBUG = os.path.join(HERE, "_lib_debug")
+LIB_DEBUG = os.path.join(OUT_DEBUG, "libnmc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -38,17 +41,19 @@ def _headers_mtime():
     return max((os.path.getmtime(p) for p in paths), default=0.0)
 
 
-def build(verbose=False, force=False):
-    """Compile and link libnmc.so; returns its path."""
-    os.makedirs(OUT, exist_ok=True)
+def build(verbose=False, force=False, debug=False):
+    """Compile and link libnmc.so (debug: the NMC_DEBUG build, in its own folder); returns its path."""
+    out, lib = (OUT_DEBUG, LIB_DEBUG) if debug else (OUT, LIB)
+    flags = FLAGS + (["-DNMC_DEBUG"] if debug else [])
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
     hdr = _headers_mtime()
     jobs = []
     for src in _sources():
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT, src[:-3] + ".o")
+        o = os.path.join(out, src[:-3] + ".o")
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
-            jobs.append([nvcc, *FLAGS, *ARCH, "-c", s, "-o", o])
+            jobs.append([nvcc, *flags, *ARCH, "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,11 +64,11 @@ def build(verbose=False, force=False):
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(OUT, src[:-3] + ".o") for src in _sources()]
-    if force or jobs or not os.path.exists(LIB):
-        run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs])
-    return LIB
+    objs = [os.path.join(out, src[:-3] + ".o") for src in _sources()]
+    if force or jobs or not os.path.exists(lib):
+        run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", lib, *objs])
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, debug="--debug" in sys.argv))

@@ -139,7 +139,26 @@ void nmc_default_params(nmc_params* p) {
 
 const char* nmc_last_error(const nmc_ctx* ctx) {
     if (!ctx) return "no context";
+#ifdef NMC_DEBUG
+    unsigned w = 0;
+    if (ctx->g.dbg && cudaMemcpy(&w, ctx->g.dbg, sizeof(w), cudaMemcpyDeviceToHost) == cudaSuccess && w != 0)
+        const_cast<nmc_ctx*>(ctx)->last_error = "NMC_DEBUG bounds check failed at site " + std::to_string(w);
+#endif
     return ctx->last_error.c_str();
+}
+
+int nmc_debug_word(nmc_ctx* ctx, uint32_t* word, int32_t clear) {
+    if (!ctx || !word) return NMC_EINVAL;
+    *word = 0;
+#ifdef NMC_DEBUG
+    cudaError_t e = cudaMemcpy(word, ctx->g.dbg, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && clear) e = cudaMemset(ctx->g.dbg, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) return set_error(ctx, NMC_ECUDA, std::string("nmc_debug_word: ") + cudaGetErrorString(e));
+    return NMC_OK;
+#else
+    (void)clear;
+    return NMC_EUNSUPPORTED;
+#endif
 }
 
 int nmc_geometric_edges(int32_t n_elem, double de1, double emax, double* edges, double* alpha) {
@@ -312,6 +331,9 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
     const size_t n_op = (size_t)ns * tb->n_ye * tb->n_t * tb->n_rho * ne;
     const size_t n_nes = (size_t)ns * tb->n_kt * tb->n_eta * ne * ne;
     const size_t n_pair = (size_t)(ns / 2) * tb->n_kt * tb->n_eta * ne * ne;
+    t.n_op = (long long)n_op;
+    t.n_nes = (long long)n_nes;
+    t.n_pair = (long long)n_pair;
     if (rc == NMC_OK) rc = upload(ctx, tb->emab, n_op, &t.emab);
     if (rc == NMC_OK) rc = upload(ctx, tb->iso, n_op, &t.iso);
     if (rc == NMC_OK) rc = upload(ctx, tb->nes, n_nes, &t.nes);
@@ -334,6 +356,29 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
         if (e != cudaSuccess) rc = NMC_ENOMEM;
         else { ctx->allocations.push_back(p); ctx->queue = static_cast<int*>(p); }
     }
+#ifdef NMC_DEBUG
+    if (rc == NMC_OK) {   // the bounds-check error word, cleared
+        void* p = nullptr;
+        e = cudaMalloc(&p, 256);
+        if (e == cudaSuccess) e = cudaMemset(p, 0, 256);
+        if (e != cudaSuccess) rc = NMC_ENOMEM;
+        else { ctx->allocations.push_back(p); ctx->g.dbg = static_cast<unsigned*>(p); }
+    }
+#endif
+    // Set-up of collision_solve_noalloc, done here because this call may allocate: load the fused
+    // kernel's variants (lazy module loading would load them at their first launch) and look up the
+    // device address of the no-allocation scratch array for this device.
+    if (rc == NMC_OK) {
+        e = preload_fused_f64_m3();
+        if (e == cudaSuccess) e = preload_fused_f64_m5();
+        if (e == cudaSuccess) e = preload_fused_f32_m3();
+        if (e == cudaSuccess) e = preload_fused_f32_m5();
+        if (e != cudaSuccess) rc = NMC_ECUDA;
+    }
+    if (rc == NMC_OK) {
+        int* scratch = nullptr;
+        rc = noalloc_scratch_address(ctx, &scratch);
+    }
     if (rc != NMC_OK) { nmc_destroy(ctx); return rc; }
     *out = ctx;
     return NMC_OK;
@@ -344,6 +389,7 @@ void nmc_destroy(nmc_ctx* ctx) {
     for (void* p : ctx->allocations) cudaFree(p);
     if (ctx->plain_scratch) cudaFree(ctx->plain_scratch);
     if (ctx->plain_counts_host) cudaFreeHost(ctx->plain_counts_host);
+    host_pipe_release(ctx);
     delete ctx;
 }
 
@@ -487,6 +533,17 @@ int opacity_interp(nmc_ctx* ctx, int32_t which, int32_t species, int64_t p, cons
     if (p == 0) return NMC_OK;
     if (!rho || !T || !Ye || !E || !out) return set_error(ctx, NMC_EINVAL, "null array argument");
     return launch_opacity_interp(ctx, which, species, p, rho, T, Ye, E, out, static_cast<cudaStream_t>(stream));
+}
+
+int opacity_interp_mixed(nmc_ctx* ctx, int32_t which, int32_t species, int64_t p, const double* rho,
+                         const double* T, const double* Ye, const double* E, double* out, void* stream) {
+    if (!ctx) return NMC_EINVAL;
+    if (which != 0 && which != 1) return set_error(ctx, NMC_EINVAL, "which must be 0 (EmAb) or 1 (Iso)");
+    if (species < 0 || species >= ctx->ns) return set_error(ctx, NMC_EINVAL, "species out of range");
+    if (p < 0) return set_error(ctx, NMC_EINVAL, "p < 0");
+    if (p == 0) return NMC_OK;
+    if (!rho || !T || !Ye || !E || !out) return set_error(ctx, NMC_EINVAL, "null array argument");
+    return launch_opacity_interp_mixed(ctx, which, species, p, rho, T, Ye, E, out, static_cast<cudaStream_t>(stream));
 }
 
 int collision_adjoint(nmc_ctx* ctx, const nmc_params* params, int64_t n, const double* rho,

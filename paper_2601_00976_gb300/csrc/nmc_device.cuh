@@ -532,6 +532,9 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
             const R mu = (R)os->mu[s], Tinv = (R)os->tinv;
             const float muh = os->mu_h[s], mul = os->mu_l[s], tih = os->tinv_h, til = os->tinv_l;
             for (int i = q; i < nqp; i += NEP) {
+                if (!NMC_IN_BOUNDS(g.dbg, (long long)((kMixed ? NS : 0) + s) * nqp + i, (long long)(kMixed ? 2 : 1) * NS * nqp,
+                                   kDbgSmemFd))
+                    continue;
                 if (kMixed) {
                     // f and 1 - f from one exp, each without cancellation.  x = (E - mu)/T reaches
                     // ~100 in the tail, where rounding x to FP32 would move exp(-|x|) by ~1e-5 in
@@ -556,7 +559,10 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         }
         __syncthreads();
         // eps^2-weighted projection and bound-enforcing limiter per (species, element)
-        if (s < NS && q < g.n_elem) {
+        if (s < NS && q < g.n_elem &&
+            NMC_IN_BOUNDS(g.dbg, ((long long)q * g.nq + g.nq - 1) * kProjQuad + kProjQuad - 1,
+                          (long long)g.n_elem * g.nq * kProjQuad, kDbgProj) &&
+            NMC_IN_BOUNDS(g.dbg, (long long)s * NEP + q * g.nq + g.nq - 1, (long long)NS * NEP, kDbgSmemVec)) {
             const int e = q, nq = g.nq;
             const R* f = fq + s * nqp + e * kProjQuad;
             const R* fc = fq + (NS + s) * nqp + e * kProjQuad;
@@ -614,16 +620,19 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         const int nr = tb.rho.n, nt = tb.t.n, ny = tb.ye.n;
         const long long base = ((((long long)s * ny + os->iy) * nt + os->it) * nr + os->ir) * NE + q;
         const long long dR = NE, dT = (long long)nr * NE, dY = (long long)nt * nr * NE;
+        const bool tab_ok = NMC_IN_BOUNDS(g.dbg, base, tb.n_op, kDbgEmabIso) &&
+                            NMC_IN_BOUNDS(g.dbg, base + dR + dT + dY, tb.n_op, kDbgEmabIso);
         const R tr = kMixed ? (R)os->wf[0] : (R)os->tr;
         const R tt = kMixed ? (R)os->wf[1] : (R)os->tt;
         const R ty = kMixed ? (R)os->wf[2] : (R)os->ty;
         // ln chi as the first corner plus weighted differences: the corners are ~ -20, so an
         // FP32 sum of the corner values themselves would round ln chi by ~2e-6 in steps
-        const R le0 = kMixed ? (R)tb.emab_f[base] : (R)tb.emab[base];
-        const R li0 = kMixed ? (R)tb.iso_f[base] : (R)tb.iso[base];
+        const R le0 = !tab_ok ? (R)0 : (kMixed ? (R)tb.emab_f[base] : (R)tb.emab[base]);
+        const R li0 = !tab_ok ? (R)0 : (kMixed ? (R)tb.iso_f[base] : (R)tb.iso[base]);
         R le = 0, li = 0;
 #pragma unroll
         for (int c8 = 1; c8 < 8; ++c8) {
+            if (!tab_ok) break;
             const int ca = c8 & 1, cb = (c8 >> 1) & 1, cc = c8 >> 2;
             const R w = (ca ? tr : (R)1 - tr) * (cb ? tt : (R)1 - tt) * (cc ? ty : (R)1 - ty);
             const long long o = base + ca * dR + cb * dT + cc * dY;
@@ -660,6 +669,9 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                     while ((r + 1) * (r + 2) / 2 <= idx) ++r;
                     const int cc = idx - r * (r + 1) / 2;
                     const long long o = off + (long long)r * NE + cc;
+                    if (!NMC_IN_BOUNDS(g.dbg, o + sT + sE, tb.n_nes, kDbgNesTable) ||
+                        !NMC_IN_BOUNDS(g.dbg, (long long)s * NE * LD + r * LD + cc, (long long)NS * NE * LD, kDbgSmemNes))
+                        continue;
                     R v;
                     if (kMixed) v = w00 * tnf[o] + w10 * tnf[o + sT] + w01 * tnf[o + sE] + w11 * tnf[o + sT + sE];
                     else v = w00 * tn[o] + w10 * tn[o + sT] + w01 * tn[o + sE] + w11 * tn[o + sT + sE];
@@ -674,6 +686,10 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                 for (int idx = (s & 1) * NEP + q; idx < NE * NE; idx += 2 * NEP) {
                     const int r = idx / NE, cc = idx - r * NE;
                     const long long o = off + idx;
+                    if (!NMC_IN_BOUNDS(g.dbg, o + sT + sE, tb.n_pair, kDbgPairTable) ||
+                        !NMC_IN_BOUNDS(g.dbg, (long long)pr * NE * LD + r * LD + cc, (long long)(NS / 2) * NE * LD,
+                                       kDbgSmemPair))
+                        continue;
                     R v;
                     if (kMixed) v = w00 * tpf[o] + w10 * tpf[o + sT] + w01 * tpf[o + sE] + w11 * tpf[o + sT + sE];
                     else v = w00 * tp[o] + w10 * tp[o + sT] + w01 * tp[o + sE] + w11 * tp[o + sT + sE];
@@ -699,6 +715,10 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                     while (cc * (cc - 1) / 2 > idx) --cc;
                     while ((cc + 1) * cc / 2 <= idx) ++cc;
                     const int r = idx - cc * (cc - 1) / 2;
+                    if (!NMC_IN_BOUNDS(g.dbg, (long long)s * NE * LD + cc * LD + r, (long long)NS * NE * LD, kDbgSmemNes) ||
+                        !NMC_IN_BOUNDS(g.dbg, (long long)s * NE * LD + r * LD + cc, (long long)NS * NE * LD, kDbgSmemNes) ||
+                        !NMC_IN_BOUNDS(g.dbg, cc, NEP, kDbgSmemVec))
+                        continue;
                     P0[r * LD + cc] = va[cc] * vai[r] * P0[cc * LD + r];
                 }
             }

@@ -33,6 +33,35 @@ constexpr double kTMin = 1.0e-3;                   // MeV, EoS range
 constexpr double kTMax = 1.0e3;
 constexpr double kCW = 4.0 * kPi / (kHC * kHC * kHC);   // 4 pi / (hc)^3  [cm^-3 MeV^-3]
 
+// Bounds checks of the NMC_DEBUG build.  Each check compares an index with
+// the length of the array it addresses; a failure records its site in the
+// context's device error word (the first failure wins), the access is skipped,
+// and the persistent kernels stop taking nodes.  Nothing traps.  In the release
+// build every check is the constant true and compiles away.
+enum DebugSite : unsigned {
+    kDbgEmabIso = 1,      // EmAb / Iso table corner (ComputeOpacities, opacity_interp)
+    kDbgNesTable = 2,     // NES table corner
+    kDbgPairTable = 3,    // pair table corner
+    kDbgSmemNes = 4,      // shared NES kernel matrix
+    kDbgSmemPair = 5,     // shared pair kernel matrix
+    kDbgSmemVec = 6,      // shared per-bin vectors
+    kDbgSmemFd = 7,       // shared Fermi--Dirac values at the projection points
+    kDbgHistory = 8,      // least-squares history (Gram matrix, outer history)
+    kDbgOutput = 9,       // per-bin output arrays
+    kDbgProj = 10,        // projection operators
+};
+
+#ifdef NMC_DEBUG
+__device__ inline bool debug_in_bounds(unsigned* word, long long idx, long long n, unsigned site) {
+    if (idx >= 0 && idx < n) return true;
+    if (word) atomicCAS(word, 0u, site);
+    return false;
+}
+#define NMC_IN_BOUNDS(word, idx, n, site) ::nmc::debug_in_bounds((word), (long long)(idx), (long long)(n), (site))
+#else
+#define NMC_IN_BOUNDS(word, idx, n, site) true
+#endif
+
 // Uniform table axis: value v maps to x = (v - lo) * inv_d with cell floor(x).
 struct Axis {
     double lo, inv_d;
@@ -59,6 +88,7 @@ struct DevGrid {
     double ends[2][kMaxNq];  // ell_p(-1/2), ell_p(+1/2)
     double sum_w2;
     double sum_wt;
+    unsigned* dbg;           // NMC_DEBUG builds: the context's bounds-check error word (null otherwise)
 };
 
 struct DevTables {
@@ -74,6 +104,7 @@ struct DevTables {
     const float* iso_f;
     const float* nes_f;
     const float* pair_f;
+    long long n_op, n_nes, n_pair;   // element counts of the EmAb/Iso, NES and pair tables
 };
 
 struct SolveArgs {
@@ -142,6 +173,19 @@ struct AdjointArgs {
 
 }  // namespace nmc
 
+namespace nmc {
+// Staging of collision_solve_host: device buffers for two chunks, the upload
+// and download streams, and per-slot events (created on the first call).
+struct HostPipe {
+    void* buf = nullptr;
+    long long chunk = 0;
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t uploaded[2] = {nullptr, nullptr};
+    cudaEvent_t solved[2] = {nullptr, nullptr};
+    cudaEvent_t downloaded[2] = {nullptr, nullptr};
+};
+}  // namespace nmc
+
 struct nmc_ctx {
     int n_elem = 0, nq = 0, ns = 0, ne = 0, nep = 0;
     std::vector<double> edges, eps, w2, w3;
@@ -155,6 +199,8 @@ struct nmc_ctx {
     void* plain_scratch = nullptr;
     size_t plain_scratch_bytes = 0;
     int* plain_counts_host = nullptr;   // pinned
+    // collision_solve_host staging
+    nmc::HostPipe host_pipe;
     // autotuned fused-kernel variants, keyed by precision, Anderson depth and block class
     std::map<int, nmc::FusedVariant> tuned;
     int device = 0;
@@ -169,6 +215,9 @@ int launch_fused(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream);
 int launch_opacity_interp(nmc_ctx* ctx, int which, int species, long long p, const double* rho,
                           const double* T, const double* Ye, const double* E, double* out,
                           cudaStream_t stream);
+int launch_opacity_interp_mixed(nmc_ctx* ctx, int which, int species, long long p, const double* rho,
+                                const double* T, const double* Ye, const double* E, double* out,
+                                cudaStream_t stream);
 size_t fused_smem_bytes(const nmc_ctx* ctx, int maxm, bool mixed, SolveArgs* a);
 int launch_adjoint(nmc_ctx* ctx, AdjointArgs& a, cudaStream_t stream);
 int launch_plain(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream);
@@ -181,9 +230,15 @@ int launch_fused_f64_m3(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, F
 int launch_fused_f64_m5(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
 int launch_fused_f32_m3(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
 int launch_fused_f32_m5(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, FusedVariant v);
+cudaError_t preload_fused_f64_m3();
+cudaError_t preload_fused_f64_m5();
+cudaError_t preload_fused_f32_m3();
+cudaError_t preload_fused_f32_m5();
+int noalloc_scratch_address(nmc_ctx* ctx, int** out);
 int autotune_fused(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, int32_t* chosen, float* chosen_ms);
 size_t adjoint_smem_bytes(const nmc_ctx* ctx, AdjointArgs* a);
 int set_error(nmc_ctx* ctx, int code, const std::string& msg);
+void host_pipe_release(nmc_ctx* ctx);
 }  // namespace nmc
 
 extern "C" int nmc_check_params_internal(nmc_ctx* ctx, const nmc_params* p);

@@ -3,10 +3,18 @@
 //
 // Some hosts own all device memory themselves: a simulation framework that
 // reserves the GPU's memory for its own pool at start-up, or an integration
-// that forbids allocation once its set-up phase is over.  After nmc_create
-// (which uploads the tables during set-up), this entry point needs no further
-// device memory: the only scratch the fused kernel uses, its work-queue
-// counter, lives in a file-scope device array instead of context memory.
+// that forbids allocation once its set-up phase is over.  The only scratch the
+// fused kernel uses, its work-queue counter, lives here in a file-scope device
+// array instead of context memory.
+//
+// Set-up happens in nmc_create, which already allocates: it looks up the
+// array's device address for the context's device and loads every fused-kernel
+// variant (under CUDA's lazy module loading a kernel's code is otherwise
+// loaded, and device memory reserved for it, at its first launch).  The
+// driver may still size its per-context local-memory reservation for the
+// kernel at the kernel's first launch on the context, so a caller that must
+// not allocate makes one call during its set-up phase (a warm-up) and any
+// number afterwards.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -29,13 +37,18 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 int* g_scratch_ptr[kMaxDevices] = {nullptr};
 
+}  // namespace
+
 // Device address of the scratch array for the current device.  The host-side
 // name g_noalloc_scratch is only a stand-in, never a device address, so the
-// address is looked up once per device with that device current.
-int scratch_address(nmc_ctx* ctx, int** out) {
+// address is looked up once per device with that device current (nmc_create
+// does it for the context's device).  The context's device must be current.
+int noalloc_scratch_address(nmc_ctx* ctx, int** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(ctx, NMC_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev != ctx->device)
+        return set_error(ctx, NMC_EINVAL, "collision_solve_noalloc: the context's device is not the current device");
     if (dev < 0 || dev >= kMaxDevices) return set_error(ctx, NMC_EUNSUPPORTED, "device index out of range");
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_scratch_ptr[dev]) {
@@ -49,7 +62,6 @@ int scratch_address(nmc_ctx* ctx, int** out) {
     return NMC_OK;
 }
 
-}  // namespace
 }  // namespace nmc
 
 using namespace nmc;
@@ -74,7 +86,7 @@ extern "C" int collision_solve_noalloc(nmc_ctx* ctx, const nmc_params* params, i
         !T_out || !n_outer || !n_inner || !status)
         return set_error(ctx, NMC_EINVAL, "null array argument");
     int* scratch = nullptr;
-    rc = scratch_address(ctx, &scratch);
+    rc = noalloc_scratch_address(ctx, &scratch);
     if (rc != NMC_OK) return rc;
     SolveArgs a{};
     a.g = ctx->g;

@@ -43,6 +43,14 @@ def node_flops(ns, ne, n_elem, nq, m, n_inner, n_outer, nes=True, pair=True):
             + 600 + 4 * ns * ne)
 
 
+def mixed_fp64_flops(ns, ne, n_outer):
+    """The part of node_flops that the mixed-precision path keeps in FP64 (the rest runs in FP32):
+    per outer iteration the EoS root find (600) and the matter sums E_nu, N_nu (4 ns ne), and once the
+    final EoS root find and the initial sums.  The inner least-squares solves are FP64 as well but
+    are not part of node_flops's count (their Gram entries are, and those are FP32)."""
+    return n_outer * (600 + 4 * ns * ne) + 600 + 4 * ns * ne
+
+
 def adjoint_flops(ns, ne, n_elem, nq, with_h=True):
     """Algorithmic flops of one node's gradient by the adjoint kernel.
 

@@ -16,7 +16,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libnmc.so")
+# NMC_DEBUG=1 in the environment selects the bounds-checked build (built by
+# `python -m paper_2601_00976_gb300._build --debug`)
+LIB_PATH = os.path.join(_HERE, "_lib_debug" if os.environ.get("NMC_DEBUG") == "1" else "_lib", "libnmc.so")
 
 NMC_OK, NMC_EINVAL, NMC_ECUDA, NMC_ENOMEM, NMC_EUNSUPPORTED = 0, 1, 2, 3, 4
 NOT_CONVERGED_INNER, NOT_CONVERGED_OUTER, NONFINITE, EOS_FAIL, TABLE_CLAMP, BAD_INPUT = 1, 2, 4, 8, 16, 32
@@ -58,7 +60,7 @@ class Params(ctypes.Structure):
 
 EXPORTS = ("nmc_default_params", "nmc_create", "nmc_destroy", "nmc_last_error", "nmc_energy_nodes",
            "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "collision_solve_noalloc", "collision_solve_v", "conserved_to_primitive",
-           "opacity_interp", "collision_adjoint", "nmc_set_plain_chunk", "nmc_autotune")
+           "opacity_interp", "collision_adjoint", "nmc_set_plain_chunk", "nmc_autotune", "nmc_fma_probe", "collision_solve_host", "opacity_interp_mixed", "nmc_debug_word")
 
 _lib = None
 
@@ -90,6 +92,8 @@ def load_library(path=LIB_PATH):
     lib.collision_solve.restype = ctypes.c_int
     lib.collision_solve_noalloc.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 16
     lib.collision_solve_noalloc.restype = ctypes.c_int
+    lib.collision_solve_host.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 15 + [ctypes.c_int64, vp]
+    lib.collision_solve_host.restype = ctypes.c_int
     lib.collision_solve_v.argtypes = ([vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 8 +
                                       [ctypes.c_int32, ctypes.c_double] + [vp] * 10)
     lib.collision_solve_v.restype = ctypes.c_int
@@ -98,12 +102,19 @@ def load_library(path=LIB_PATH):
     lib.conserved_to_primitive.restype = ctypes.c_int
     lib.opacity_interp.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64] + [vp] * 6
     lib.opacity_interp.restype = ctypes.c_int
+    lib.opacity_interp_mixed.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64] + [vp] * 6
+    lib.opacity_interp_mixed.restype = ctypes.c_int
     lib.collision_adjoint.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 20
     lib.collision_adjoint.restype = ctypes.c_int
     lib.nmc_autotune.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64] + [vp] * 18
     lib.nmc_autotune.restype = ctypes.c_int
     lib.nmc_set_plain_chunk.argtypes = [vp, ctypes.c_int64]
     lib.nmc_set_plain_chunk.restype = ctypes.c_int
+    lib.nmc_fma_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp,
+                                  ctypes.POINTER(ctypes.c_double), vp]
+    lib.nmc_fma_probe.restype = ctypes.c_int
+    lib.nmc_debug_word.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32]
+    lib.nmc_debug_word.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -140,6 +151,20 @@ def grid_nodes(edges, n_q):
     if rc != NMC_OK:
         raise ValueError(f"nmc_grid_nodes failed ({rc})")
     return eps, w2, w3
+
+
+def fma_probe(precision, iters, sink, blocks_per_sm=0, stream=None):
+    """Launch the FMA-pipe peak probe on `stream` (torch's current one by default); returns the
+    launch's flop count.  sink: a one-element CUDA tensor of the precision's dtype."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    flops = ctypes.c_double()
+    rc = load_library().nmc_fma_probe(int(precision), int(blocks_per_sm), int(iters),
+                                      ctypes.c_void_p(sink.data_ptr()), ctypes.byref(flops),
+                                      ctypes.c_void_p(s.cuda_stream))
+    if rc != NMC_OK:
+        raise NmcError(f"nmc_fma_probe failed with code {rc}")
+    return flops.value
 
 
 def _dptr(a):
@@ -200,6 +225,13 @@ class Context:
     def last_error(self):
         return self._lib.nmc_last_error(self._h).decode()
 
+    def debug_word(self, clear=False):
+        """The NMC_DEBUG build's bounds-check error word (0: no check failed); raises NmcError on a
+        release build."""
+        w = ctypes.c_uint32()
+        self._check(self._lib.nmc_debug_word(self._h, ctypes.byref(w), 1 if clear else 0), "nmc_debug_word")
+        return int(w.value)
+
     def _check(self, rc, what):
         if rc != NMC_OK:
             raise NmcError(f"{what} failed with code {rc}: {self.last_error()}")
@@ -246,6 +278,40 @@ class Context:
         self._check(rc, "collision_solve")
         if host:
             out = {k: v.to("cpu", non_blocking=False) for k, v in out.items()}
+        return out
+
+    def host_outputs(self, n):
+        """Page-locked host tensors for the outputs of collision_solve_host on n nodes."""
+        import torch
+        ns, ne = self.n_species, self.ne
+        f64 = dict(dtype=torch.float64, pin_memory=True)
+        i32 = dict(dtype=torch.int32, pin_memory=True)
+        return dict(J=torch.empty((n, ns, ne), **f64), H=torch.empty((n, ns, ne, 3), **f64),
+                    Ye=torch.empty(n, **f64), eps=torch.empty(n, **f64), T=torch.empty(n, **f64),
+                    n_outer=torch.empty(n, **i32), n_inner=torch.empty(n, **i32), status=torch.empty(n, **i32))
+
+    def collision_solve_host(self, params, inp, out, chunk=0, stream=None, sync=True):
+        """collision_solve_host on CPU tensors: inp holds rho, T, Ye, D (J), I (H), dt and optionally scale
+        (contiguous float64, page-locked for overlapped copies); out is a dict like host_outputs(n).
+        The copies and the solve are pipelined by the library; with sync the call waits for `stream`."""
+        import torch
+        x = [inp[k] for k in ("rho", "T", "Ye", "D", "I", "dt")] + [inp.get("scale")]
+        for v in x + list(out.values()):
+            if v is not None and (v.is_cuda or not v.is_contiguous()):
+                raise ValueError("collision_solve_host takes contiguous CPU tensors")
+        n = inp["rho"].shape[0]
+        ns, ne = self.n_species, self.ne
+        if inp["D"].shape != (n, ns, ne) or inp["I"].shape != (n, ns, ne, 3):
+            raise ValueError(f"D must be {(n, ns, ne)} and I {(n, ns, ne, 3)}")
+        p = lambda v: ctypes.c_void_p(v.data_ptr()) if v is not None else None  # noqa: E731
+        s = self._stream_handle(stream)
+        rc = self._lib.collision_solve_host(
+            self._h, ctypes.byref(params), n, *[p(v) for v in x],
+            p(out["J"]), p(out["H"]), p(out["Ye"]), p(out["eps"]), p(out["T"]),
+            p(out["n_outer"]), p(out["n_inner"]), p(out["status"]), int(chunk), s)
+        self._check(rc, "collision_solve_host")
+        if sync:
+            (stream if stream is not None else torch.cuda.current_stream()).synchronize()
         return out
 
     def collision_solve_v(self, params, rho, T, Ye, v, J, H, dt, scale=None, freeze_velocity=False,
@@ -359,12 +425,17 @@ class Context:
         """Chunk size (nodes) of the plain per-iteration mode."""
         self._check(self._lib.nmc_set_plain_chunk(self._h, int(nodes)), "nmc_set_plain_chunk")
 
-    def opacity_interp(self, which, species, rho, T, Ye, E, out=None, stream=None):
+    def opacity_interp(self, which, species, rho, T, Ye, E, out=None, stream=None, mixed=False):
+        """chi_EmAb (which = 0) or sigma_Iso (1) of `species` at points (rho, T, Ye, E): CUDA float64
+        tensors of one length.  mixed=True runs opacity_interp_mixed (FP32 arithmetic)."""
         import torch
+        for x in (rho, T, Ye, E):
+            if x.dtype != torch.float64 or not x.is_contiguous() or not x.is_cuda or x.shape != rho.shape:
+                raise ValueError("points must be contiguous CUDA float64 tensors of one length")
         if out is None:
             out = torch.empty_like(rho)
         p = lambda x: ctypes.c_void_p(x.data_ptr())  # noqa: E731
-        rc = self._lib.opacity_interp(self._h, which, species, rho.shape[0], p(rho), p(T), p(Ye), p(E), p(out),
-                                      self._stream_handle(stream))
-        self._check(rc, "opacity_interp")
+        fn = self._lib.opacity_interp_mixed if mixed else self._lib.opacity_interp
+        rc = fn(self._h, which, species, rho.shape[0], p(rho), p(T), p(Ye), p(E), p(out), self._stream_handle(stream))
+        self._check(rc, "opacity_interp_mixed" if mixed else "opacity_interp")
         return out

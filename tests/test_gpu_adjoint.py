@@ -1,17 +1,15 @@
 """GPU collision_adjoint: parity with the oracle's IFT gradient, finite
 differences of GPU forward solves, the autograd Function, and edge cases.
 
-The bar is 1e-6 relative for every gradient group (per node, relative to the
-group's largest entry, plus 1e-5 per entry on the entries that carry it): the
-oracle forms every derivative by fourth-order central differences, the GPU
-forms dQ/dD analytically and dQ/dy by second-order differences with 1e-6
-steps, so both sit ~1e-9 from the exact gradient.  On top of that each entry
-may move by 10 * tol * cond * mag: the two sides differentiate at two
-converged solutions that differ by up to the forward tolerance tol, and an
-IFT gradient moves by cond(dG/dD) * |dD| times the size of the terms it is
-summed from (mag, reported by the oracle).  Optically thick nodes
-(rho > 1e14) have cond ~ 1e8: number-conserving NES and pair couplings leave
-the lepton-number mode with a singular value ~1 / (1 + dtau chi).
+Parity with the oracle: collision_adjoint takes the converged moments as an
+input, so it is given the oracle's own converged D (and T) for the compared
+nodes, and both sides differentiate the same root at the same point.  The
+bar is 1e-6 relative for every gradient group (per node, relative to the
+group's largest entry, plus 1e-5 per entry on the entries that carry it),
+with no allowance for the forward solve: the oracle forms every derivative
+by fourth-order central differences, the GPU forms dQ/dD analytically and
+dQ/dy by second-order differences with 1e-6 steps, so both sit ~1e-9 from
+the exact gradient.
 """
 
 import numpy as np
@@ -46,28 +44,45 @@ def _adjoint(ctx, p, t, fw, ct):
     return {k: v.cpu().numpy() for k, v in g.items()}
 
 
-def _assert_group(a, b, allow, what, n):
-    """a (GPU) against b (oracle) for one gradient group of node n; allow is the
-    per-entry allowance for the forward solutions' difference."""
-    a, b, allow = (np.asarray(x, dtype=float) for x in (a, b, allow))
+def _at_oracle_root(t, nodes, res):
+    """The nodes' inputs, with J_out and T_out set to the oracle's converged D and T (res: oracle
+    (solve, gradient) pairs), so that the GPU adjoint differentiates at the oracle's point."""
+    idx = torch.tensor(nodes, device=t["rho"].device)
+    sub = {k: v[idx].contiguous() for k, v in t.items()}
+    fw = dict(J=torch.tensor(np.stack([r["D"] for r, _ in res]), dtype=torch.float64, device=t["rho"].device),
+              T=torch.tensor([r["T"] for r, _ in res], dtype=torch.float64, device=t["rho"].device))
+    return sub, fw
+
+
+def _assert_group(a, b, what, n):
+    """a (GPU) against b (oracle) for one gradient group of node n."""
+    a, b = (np.asarray(x, dtype=float) for x in (a, b))
     ref = np.max(np.abs(b))
     err = np.abs(a - b)
-    assert np.all(err <= GRAD_TOL * ref + allow + 1e-300), (what, n, np.max(err) / max(ref, 1e-300))
+    assert np.all(err <= GRAD_TOL * ref + 1e-300), (what, n, np.max(err) / max(ref, 1e-300))
     big = np.abs(b) >= 1e-3 * ref
-    assert np.all(err[big] <= 1e-5 * np.abs(b[big]) + allow[big]), (what, n)
+    assert np.all(err[big] <= 1e-5 * np.abs(b[big])), (what, n)
 
 
-def _compare(gg, n, r_or, g_or, tol_fw):
-    assert int(gg["status"][n]) in OK_STATUS, (n, gg["status"][n])
-    k = 10.0 * tol_fw * g_or["cond"]
-    m = g_or["mag"]
-    _assert_group(gg["J"][n], g_or["D_star"], k * m["D_star"], "D*", n)
-    _assert_group(gg["H"][n], g_or["I_star"], k * m["I_star"], "I*", n)
-    _assert_group(gg["scale"][n], g_or["scale"], k * m["scale"], "scale", n)
+def _compare(gg, i, r_or, g_or, n=None):
+    """GPU gradients of row i against the oracle's gradient of node n (default i)."""
+    n = i if n is None else n
+    assert int(gg["status"][i]) in OK_STATUS, (n, gg["status"][i])
+    _assert_group(gg["J"][i], g_or["D_star"], "D*", n)
+    _assert_group(gg["H"][i], g_or["I_star"], "I*", n)
+    _assert_group(gg["scale"][i], g_or["scale"], "scale", n)
     sT = r_or["T"] / r_or["Ye"]
-    _assert_group([gg["Ye"][n], gg["T"][n] * sT], [g_or["Ye"], g_or["T"] * sT],
-                  [k * m["Ye"], k * m["T"] * sT], "Ye,T", n)
-    assert abs(gg["T"][n] - g_or["T"]) <= 1e-5 * abs(g_or["T"]) + k * m["T"]
+    _assert_group([gg["Ye"][i], gg["T"][i] * sT], [g_or["Ye"], g_or["T"] * sT], "Ye,T", n)
+    assert abs(gg["T"][i] - g_or["T"]) <= 1e-5 * abs(g_or["T"])
+
+
+def _oracle_parity(ctx, p, t, ct, nodes, res):
+    """GPU adjoint at the oracle's converged point of each node, against the oracle's gradient."""
+    sub, fw = _at_oracle_root(t, nodes, res)
+    gg = _adjoint(ctx, p, sub, fw, {k: v[nodes] for k, v in ct.items()})
+    for i, (n, (r, go)) in enumerate(zip(nodes, res)):
+        assert r["status"] == 0
+        _compare(gg, i, r, go, n)
 
 
 def _oracle_tasks(case, inp, nodes, ct, params):
@@ -82,13 +97,10 @@ def test_adjoint_matches_oracle_gradient_small_grid(frozen):
     edges, g, tables, inp = make_case(4, 20.0, 2, 2, "profile", 12, seed=40 + frozen, table_seed=6)
     ctx = nmc.Context(edges, 2, 2, tables)
     t = to_device(inp)
-    p, fw = _forward(ctx, t, frozen_matter=frozen, **TIGHT)
+    p = nmc.default_params(frozen_matter=frozen, **TIGHT)
     ct = oracle_pool.cotangents(np.random.default_rng(5 + frozen), 12, 2, g.ne)
-    gg = _adjoint(ctx, p, t, fw, ct)
     res = oracle_pool.run(_oracle_tasks(case, inp, range(12), ct, dict(frozen_matter=frozen, **ORACLE_TIGHT)))
-    for n, (r, go) in enumerate(res):
-        assert r["status"] == 0
-        _compare(gg, n, r, go, TIGHT["tol_inner"])
+    _oracle_parity(ctx, p, t, ct, list(range(12)), res)
     ctx.close()
 
 
@@ -100,15 +112,12 @@ def test_adjoint_matches_oracle_gradient_four_species_grid_c():
     edges, g, tables, inp = make_case(16, 1.875, 2, 4, "profile", N, seed=11, table_seed=0)
     ctx = nmc.Context(edges, 2, 4, tables)
     t = to_device(inp)
-    p, fw = _forward(ctx, t, **TIGHT)
+    p = nmc.default_params(**TIGHT)
     ct = oracle_pool.cotangents(np.random.default_rng(17), N, 4, g.ne)
-    gg = _adjoint(ctx, p, t, fw, ct)
     order = np.argsort(inp["rho"])
     nodes = [int(order[i]) for i in np.linspace(0, N - 1, 6).astype(int)]
     res = oracle_pool.run(_oracle_tasks(case, inp, nodes, ct, ORACLE_TIGHT))
-    for n, (r, go) in zip(nodes, res):
-        assert r["status"] == 0
-        _compare(gg, n, r, go, TIGHT["tol_inner"])
+    _oracle_parity(ctx, p, t, ct, nodes, res)
     ctx.close()
 
 
@@ -132,10 +141,12 @@ def test_adjoint_matches_finite_differences_of_gpu_solves():
     outputs are linear in it) and in the scale factors (the solve is a smooth function of them on
     the scale of s itself).  Bar: |fd - ad| <= 1e-6 * S + F, with S the sum of |terms| of <grad, v>
     and F = 1e-11 |L|_1 / h, the rounding of forward solves converged to 1e-13 (a difference
-    quotient cannot resolve less).  A forward solve's error grows with cond(dG/dD) along the
-    lepton-number mode of optically thick nodes, so a node over that bar is re-checked with
-    F + 10 tol cond |L|_1 / h, cond from the oracle's Jacobian at that node; at most 10% of the
-    nodes may need it."""
+    quotient cannot resolve less).  Nodes within 2e-3 cell widths of a table face (the tables are
+    piecewise linear there) or with a flagged status are left out and counted.  A forward solve's
+    error grows with cond(dG/dD) along the lepton-number mode of optically thick nodes, so a
+    difference quotient there can miss the bar without the gradient being wrong: every node over
+    the bar is re-checked against the oracle's gradient at the oracle's converged point, at the
+    strict 1e-6 bar; at most 10% of the nodes may need it."""
     N = 256
     edges, g, tables, inp = make_case(16, 1.875, 2, 4, "profile", N, seed=23, table_seed=0)
     ctx = nmc.Context(edges, 2, 4, tables)
@@ -187,17 +198,15 @@ def test_adjoint_matches_finite_differences_of_gpu_solves():
         assert ok.sum() >= 0.9 * N, (name, ok.sum())
         over += [(name, int(i), err[i], GRAD_TOL * S[i] + F[i], h) for i in np.nonzero(bad)[0]]
     nodes = sorted({o[1] for o in over})
+    report.append(f"left out: {int(np.count_nonzero(near))} near a table face; "
+                  f"re-checked against the oracle's gradient: {len(nodes)}")
     print("\n".join(report))
     assert len(nodes) <= 0.1 * N, (len(nodes), report)
     if nodes:
-        tasks = [dict(case=(16, 1.875, 2, 4, 0), x=oracle_pool.node_slice(inp, i), params=ORACLE_TIGHT)
-                 for i in nodes]
-        cond = dict(zip(nodes, oracle_pool.run(tasks, fn=oracle_pool.node_condition)))
         for name, i, e, bar, h in over:
-            extra = 10.0 * TIGHT["tol_inner"] * cond[i] * Lmag[i] / h
-            print(f"{name} node {i}: rho {inp['rho'][i]:.3g} cond {cond[i]:.3g} err {e:.3g} bar {bar:.3g} "
-                  f"+ {extra:.3g}")
-            assert e <= bar + extra, (name, i, e, bar, extra)
+            print(f"{name} node {i}: rho {inp['rho'][i]:.3g} err {e:.3g} bar {bar:.3g}")
+        res = oracle_pool.run(_oracle_tasks((16, 1.875, 2, 4, 0), inp, nodes, ct, ORACLE_TIGHT))
+        _oracle_parity(ctx, p, t, ct, nodes, res)
     ctx.close()
 
 
@@ -265,7 +274,8 @@ def test_adjoint_edge_cases():
 
 def test_adjoint_full_size_sampled_against_oracle():
     """2^18 nodes of the adjoint workload (4 species, 16 x 2 energies, profile) at the benchmark's
-    tolerance: every gradient finite with a clean status, and 4 sampled nodes against the oracle."""
+    tolerance: every node converged, every gradient finite with a clean status, and 4 sampled nodes
+    against the oracle's gradient at the oracle's converged point."""
     N = 1 << 18
     case = (16, 1.875, 2, 4, 0)
     edges, g, tables, inp = make_case(16, 1.875, 2, 4, "profile", N, seed=5, table_seed=0)
@@ -275,15 +285,12 @@ def test_adjoint_full_size_sampled_against_oracle():
     ct = oracle_pool.cotangents(np.random.default_rng(8), N, 4, g.ne)
     gg = _adjoint(ctx, p, t, fw, ct)
     st_fw = fw["status"].cpu().numpy()
-    conv = np.isin(st_fw, OK_STATUS)
-    assert conv.mean() > 0.99
-    assert np.all(np.isin(gg["status"][conv], OK_STATUS))
+    assert np.count_nonzero(st_fw) == 0, np.unique(st_fw, return_counts=True)
+    assert np.count_nonzero(gg["status"]) == 0, np.unique(gg["status"], return_counts=True)
     for k in ("J", "H", "Ye", "T", "scale"):
-        assert np.all(np.isfinite(gg[k][conv])), k
+        assert np.all(np.isfinite(gg[k])), k
     rng = np.random.default_rng(12)
-    nodes = [int(n) for n in rng.choice(np.nonzero(conv)[0], size=4, replace=False)]
+    nodes = [int(n) for n in rng.choice(N, size=4, replace=False)]
     res = oracle_pool.run(_oracle_tasks(case, inp, nodes, ct, ORACLE_TIGHT))
-    for n, (r, go) in zip(nodes, res):
-        assert r["status"] == 0
-        _compare(gg, n, r, go, 1e-10)
+    _oracle_parity(ctx, p, t, ct, nodes, res)
     ctx.close()

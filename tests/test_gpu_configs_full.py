@@ -2,11 +2,13 @@
 
 * Mixed precision: 2^20 perturbed-profile nodes, 4 species, 32 linear elements
   (64 energies); the mixed solve against the FP64 GPU solve (tol 1e-12) on the same inputs for
-  every node, species and matter output (<= 1e-5), and sampled nodes against the oracle.  The
-  mixed solve runs at tol 1e-10: the perturbed profile's stiffest nodes keep an error
-  ~ tol (1 + dtau chi) in the number-conserving mode (a change-based stop at tol leaves the
-  slowest mode off by tol over its contraction gap), 1.04e-5 at tol 3e-10 and 6.3e-7 at 1e-10
-  on this batch.
+  every node, species and matter output, in the W2 norm and bin by bin (<= 1e-5), and sampled
+  nodes against the oracle.  The mixed solve runs at tol 1e-10 inner and 1e-9 outer, as the
+  benchmark does: where dtau chi ~ 1e4 the heavy flavours' number-conserving mode keeps an error
+  ~ tol_inner (1 + dtau chi), which needs tol_inner 1e-10 for 1e-5 on this batch; an outer test at
+  1e-10 chases the FP32 rounding of the converged moments (q moves by ~1e-10 relative between
+  outer iterations) and 142 of the 2^20 nodes cycled to the outer cap, none at 1e-9.  Every node
+  converges: the status counts are exact.
 * Uneven batch: 2^22 core/tail nodes (half rho > 1e13, half rho < 1e10, dt log-uniform
   1e-7..1e-5 s), FP64, the autotuned persistent kernel: every node converges, lepton number and
   energy are conserved to 1e-12, and sampled nodes match the oracle.
@@ -19,7 +21,7 @@ import torch
 from oracle import solver as osolver, eos as oeos
 from oracle.constants import M_B, MEV_TO_ERG, lepton_numbers
 from paper_2601_00976_gb300 import nmc
-from gpu_helpers import make_case, to_device, wnorm_errors, compare_node
+from gpu_helpers import make_case, to_device, wnorm_errors, compare_node, assert_bins, bin_errors_t, BIN_FLOOR_MIXED
 
 pytestmark = pytest.mark.gpu
 
@@ -39,14 +41,17 @@ def test_mixed_full_size_64_energies_against_fp64_and_oracle():
     ctx = nmc.Context(edges, 2, 4, tables)
     t = to_device(inp)
     del inp["I"]
-    mix = _solve(ctx, t, precision=nmc.MIXED, tol_inner=1e-10, tol_outer=1e-10)
+    mix = _solve(ctx, t, precision=nmc.MIXED, tol_inner=1e-10, tol_outer=1e-9)
     f64 = _solve(ctx, t, tol_inner=1e-12, tol_outer=1e-12)
-    ok = ((mix["status"] == 0) & (f64["status"] == 0))
-    assert ok.float().mean().item() > 0.999
+    for o in (mix, f64):
+        assert int(torch.count_nonzero(o["status"]).item()) == 0, torch.unique(o["status"], return_counts=True)
+    ok = torch.ones(N, dtype=torch.bool, device="cuda")
     w2 = torch.tensor(g.W2, device="cuda")
     ref = torch.sqrt(torch.sum(w2 * f64["J"][ok] ** 2, dim=-1))
     eD = torch.sqrt(torch.sum(w2 * (mix["J"][ok] - f64["J"][ok]) ** 2, dim=-1)) / ref
     assert eD.max().item() <= 1e-5, eD.max(dim=0).values.tolist()
+    bD, bI = bin_errors_t(mix["J"], mix["H"], f64["J"], f64["H"], BIN_FLOOR_MIXED)
+    assert bD.max().item() <= 1e-5 and bI.max().item() <= 1e-5, (bD.tolist(), bI.tolist())
     for k in ("Ye", "eps", "T"):
         e = torch.max(torch.abs(mix[k][ok] - f64[k][ok]) / torch.abs(f64[k][ok])).item()
         assert e <= 1e-5, (k, e)
@@ -61,6 +66,7 @@ def test_mixed_full_size_64_energies_against_fp64_and_oracle():
     for i, r in enumerate(refs):
         eDn, _ = wnorm_errors(out["J"][i], out["H"][i], r["D"], r["I"], g.W2)
         assert eDn.max() <= 1e-5, (nodes[i], eDn)
+        assert_bins(out["J"][i], out["H"][i], r["D"], r["I"], 1e-5, BIN_FLOOR_MIXED, what=nodes[i])
         for k in ("Ye", "eps", "T"):
             assert abs(out[k][i] - r[k]) <= 1e-5 * abs(r[k])
     ctx.close()
@@ -76,7 +82,7 @@ def test_uneven_core_tail_full_size_fp64():
                  t["I"][:1 << 16], t["dt"][:1 << 16], t["scale"][:1 << 16])
     out = _solve(ctx, t)
     st = out["status"].cpu().numpy()
-    assert np.count_nonzero(st) <= N // 10000, np.unique(st, return_counts=True)
+    assert np.count_nonzero(st) == 0, np.unique(st, return_counts=True)
     ni = out["n_inner"].cpu().numpy()
     assert ni.min() <= 5 and ni.max() >= 60   # the uneven mix this workload is for
     # conservation of lepton number and energy, every converged node (FP64 sums on the device)
@@ -98,6 +104,7 @@ def test_uneven_core_tail_full_size_fp64():
         # the GPU stops at tol 1e-10 (the oracle at 1e-13); optically thick nodes carry tol (1 + dtau chi) in the
         # number-conserving mode
         assert eDn.max() <= 1e-5, (nodes[i], eDn)
+        assert_bins(o["J"][i], o["H"][i], r["D"], r["I"], 1e-5, BIN_FLOOR_MIXED, what=nodes[i])
         for k in ("Ye", "eps"):
             assert abs(o[k][i] - r[k]) <= 1e-7 * abs(r[k])
         E0 = inp["rho"][nodes[i]] * oeos.specific_energy(inp["rho"][nodes[i]], inp["T"][nodes[i]], inp["Ye"][nodes[i]]) \

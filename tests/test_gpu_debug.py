@@ -1,0 +1,79 @@
+"""The NMC_DEBUG build on the GPU: well-formed calls of every kernel family leave the bounds-check
+error word clear and give the release build's results.
+
+The debug library is loaded in a child process (NMC_DEBUG=1 selects it), so that the two builds
+never share a process; the child prints its results as JSON.
+"""
+
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+pytestmark = pytest.mark.gpu
+
+CHILD = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1]); sys.path.insert(0, sys.argv[1] + "/tests")
+from paper_2601_00976_gb300 import nmc, synthetic
+from gpu_helpers import make_case, to_device
+res = {"lib": nmc.LIB_PATH}
+for n_elem, de1, kind in ((16, 1.875, "profile"), (32, 1.0, "perturbed")):
+    edges, g, tables, inp = make_case(n_elem, de1, 2, 4, kind, 96, seed=7)
+    ctx = nmc.Context(edges, 2, 4, tables)
+    t = to_device(inp)
+    for name, kw in (("fp64", {}), ("mixed", dict(precision=nmc.MIXED)), ("plain", dict(mode=nmc.MODE_PLAIN))):
+        o = ctx.collision_solve(nmc.default_params(**kw), t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+        torch.cuda.synchronize()
+        res[f"{n_elem}_{name}_J"] = o["J"].cpu().numpy().ravel()[::37].tolist()
+        res[f"{n_elem}_{name}_status"] = o["status"].cpu().numpy().tolist()
+    for mixed in (False, True):
+        v = ctx.opacity_interp(0, 1, t["rho"], t["T"], t["Ye"], t["rho"] * 0 + 10.0, mixed=mixed)
+        res[f"{n_elem}_interp_{int(mixed)}"] = v.cpu().numpy().tolist()
+    if n_elem == 16:
+        vel = torch.tensor(synthetic.make_velocities("profile", 96, seed=8), device="cuda")
+        ov = ctx.collision_solve_v(nmc.default_params(), t["rho"], t["T"], t["Ye"], vel, t["D"], t["I"], t["dt"], t["scale"])
+        fw = ctx.collision_solve(nmc.default_params(), t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+        ga = ctx.collision_adjoint(nmc.default_params(), t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"],
+                                   fw["J"], fw["T"], gJ=torch.ones_like(t["D"]))
+        c2 = ctx.conserved_to_primitive(t["D"], t["I"], vel)
+        torch.cuda.synchronize()
+        res["v_J"] = ov["J"].cpu().numpy().ravel()[::37].tolist()
+        res["adj_J"] = ga["J"].cpu().numpy().ravel()[::37].tolist()
+        res["c2p_D"] = c2["D"].cpu().numpy().ravel()[::37].tolist()
+    res[f"{n_elem}_word"] = ctx.debug_word() if nmc.LIB_PATH.endswith("_lib_debug/libnmc.so") else 0
+    ctx.close()
+print(json.dumps(res))
+"""
+
+
+def _run(debug):
+    env = dict(os.environ)
+    env.pop("NMC_DEBUG", None)
+    if debug:
+        env["NMC_DEBUG"] = "1"
+    r = subprocess.run([sys.executable, "-c", CHILD, ROOT], capture_output=True, text=True, env=env, timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_debug_build_checks_stay_clear_and_match_release():
+    from paper_2601_00976_gb300 import _build
+    _build.build(debug=True)
+    dbg, rel = _run(True), _run(False)
+    assert dbg["lib"].endswith("_lib_debug/libnmc.so") and rel["lib"].endswith("_lib/libnmc.so")
+    assert dbg["16_word"] == 0 and dbg["32_word"] == 0, (dbg["16_word"], dbg["32_word"])
+    for k, v in rel.items():
+        if k == "lib" or k.endswith("_word"):
+            continue
+        a, b = np.asarray(dbg[k]), np.asarray(v)
+        if k.endswith("status"):
+            assert np.array_equal(a, b), k
+        else:   # the checks add branches, not arithmetic; compilation may still reorder an FMA
+            assert np.allclose(a, b, rtol=1e-9, atol=0), (k, np.max(np.abs(a - b) / np.abs(b)))

@@ -3,7 +3,8 @@ moment, conservation sums, matter update and least-squares solves) against the
 FP64 oracle.
 
 Target: <= 1e-5 relative error in D (per species, W2-weighted norm relative to
-||D_ref||), Ye, eps and T for every species, with conservation of lepton number
+||D_ref||, and bin by bin with the mixed floor of gpu_helpers), I, Ye, eps and T
+for every species, with conservation of lepton number
 and energy held to 1e-12 relative (the matter state is formed in FP64 from the
 returned moments).  The oracle runs at 1e-13.
 
@@ -21,7 +22,7 @@ import pytest
 from oracle import solver as osolver, eos as oeos
 from oracle.constants import M_B, MEV_TO_ERG, lepton_numbers
 from paper_2601_00976_gb300 import nmc
-from gpu_helpers import make_case, gpu_solve, wnorm_errors
+from gpu_helpers import make_case, gpu_solve, wnorm_errors, assert_bins, bin_errors, BIN_FLOOR_MIXED
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +39,7 @@ def _check(out, ref, nodes, W2, target):
         errs = [eD.max(), eI.max()] + [abs(out[k][n] - r[k]) / abs(r[k]) for k in ("Ye", "eps", "T")]
         worst = max(worst, max(errs))
         assert max(errs) <= target, (n, errs)
+        assert_bins(out["J"][n], out["H"][n], r["D"], r["I"], target, BIN_FLOOR_MIXED, what=n)
     return worst
 
 
@@ -91,10 +93,13 @@ def test_mixed_full_size_vs_fp64_gpu():
     ctx = nmc.Context(edges, 2, 4, tables)
     mix = gpu_solve(ctx, inp, **MIXED)
     f64 = gpu_solve(ctx, inp, tol_inner=1e-12, tol_outer=1e-12)
-    ok = (mix["status"] == 0) & (f64["status"] == 0)
-    assert ok.mean() > 0.999
+    assert np.count_nonzero(mix["status"]) == 0, np.unique(mix["status"], return_counts=True)
+    assert np.count_nonzero(f64["status"]) == 0, np.unique(f64["status"], return_counts=True)
+    ok = np.ones(N, dtype=bool)
     eD, _ = wnorm_errors(mix["J"][ok], mix["H"][ok], f64["J"][ok], f64["H"][ok], g.W2)
     assert eD.max() <= TARGET, eD.max(axis=0)
+    bD, bI = bin_errors(mix["J"], mix["H"], f64["J"], f64["H"], BIN_FLOOR_MIXED)
+    assert bD.max() <= TARGET and bI.max() <= TARGET, (bD.max(), bI.max())
     for k in ("Ye", "eps", "T"):
         assert np.max(np.abs(mix[k][ok] - f64[k][ok]) / np.abs(f64[k][ok])) <= TARGET, k
     ctx.close()

@@ -6,7 +6,7 @@ forward-peaked initial distribution, Grid C (16 linear elements), tol 1e-8, M_in
 dt from 1e-4 ms growing by 1.04 per step to t = 100 ms (271 steps).
 
 * The first steps follow the oracle's backward-Euler trajectory (oracle/velocity.py step by step)
-  to 1e-9 at tol 1e-12 on both sides.
+  to 1e-9 at tol 1e-12 on both sides (W2 norms and bin by bin).
 * Both tests run fully implicit and semi-implicit (opacities at each step's old state, Sec. 3.5);
   every step conserves in either, and both relax to the same equilibrium.
 * Over the whole run every step converges; total lepton number and total energy are conserved
@@ -24,6 +24,7 @@ import torch
 from oracle import grid as ogrid, solver as osolver, velocity as ovel, eos as oeos
 from oracle.equilibrium import equilibrium_distribution
 from paper_2601_00976_gb300 import nmc, synthetic, relaxation
+from gpu_helpers import assert_bins, BIN_FLOOR_FP64
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +63,7 @@ def test_first_steps_follow_the_oracle(semi):
         eD = np.sqrt(np.sum(g.W2 * (s["J"] - r["D"]) ** 2, axis=-1)) / ref
         eI = np.sqrt(np.sum(g.W2[:, None] * (s["H"] - r["I"]) ** 2, axis=(-2, -1))) / ref
         assert np.all(eD <= 1e-9) and np.all(eI <= 1e-9), (dt, eD, eI)
+        assert_bins(s["J"], s["H"], r["D"], r["I"], 1e-9, BIN_FLOOR_FP64, what=dt)
         assert np.max(np.abs(s["v"] - r["v"])) <= 1e-12
         for k in ("Ye", "T", "eps"):
             assert abs(s[k] - r[k]) <= 1e-9 * abs(r[k]), (k, s[k], r[k])

@@ -251,6 +251,16 @@ def test_opacity_interp_parity(case2):
     for which in (0, 1):
         for sp in range(4):
             out = ctx.opacity_interp(which, sp, dev["rho"], dev["T"], dev["Ye"], dev["E"]).cpu().numpy()
+            # the FP32 entry point: FP32 ln tables, logarithms, weights and exp (~1e-6 relative)
+            mx = ctx.opacity_interp(which, sp, dev["rho"], dev["T"], dev["Ye"], dev["E"], mixed=True).cpu().numpy()
             for i in range(0, P, 97):
                 r = oop.opacity_at(tables, which, sp, rho[i], T[i], Ye[i], E[i])
                 assert out[i] == pytest.approx(r, rel=1e-12), (which, sp, i)
+                assert mx[i] == pytest.approx(r, rel=1e-5), (which, sp, i, mx[i], r)
+    # empty batches are no-ops; bad selectors are argument errors
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    assert ctx.opacity_interp(0, 0, e, e, e, e, mixed=True).numel() == 0
+    with pytest.raises(nmc.NmcError):
+        ctx.opacity_interp(2, 0, dev["rho"], dev["T"], dev["Ye"], dev["E"], mixed=True)
+    with pytest.raises(nmc.NmcError):
+        ctx.opacity_interp(0, 4, dev["rho"], dev["T"], dev["Ye"], dev["E"], mixed=True)

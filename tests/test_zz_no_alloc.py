@@ -4,7 +4,8 @@ The no-allocation entry point serves callers that cannot allocate device
 memory when they solve (their memory is owned by another allocator after
 set-up).  It must give the same results as collision_solve; it is called twice
 in a row because its static work counter keeps the previous call's value and
-must be cleared by each call.  This file is collected last on purpose.
+must be cleared by each call, and the second call must leave the device's free
+memory unchanged.  This file is collected last on purpose.
 """
 
 import ctypes
@@ -49,10 +50,15 @@ def test_noalloc_matches_collision_solve_twice(precision):
     prm = nmc.default_params(**kw)
     ref = _outputs(N, 4, ctx.ne)
     _call(L.collision_solve, ctx, prm, t, ref)
-    for _ in range(2):
+    for call in range(2):
         out = _outputs(N, 4, ctx.ne)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         _call(L.collision_solve_noalloc, ctx, prm, t, out)
         torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        if call == 1:   # after a warm-up call, a call takes no device memory (cudaMemGetInfo)
+            assert free1 == free0, (free0, free1)
         for k in ("J", "H", "Ye", "eps", "T"):
             a, b = out[k].cpu().numpy(), ref[k].cpu().numpy()
             assert np.allclose(a, b, rtol=1e-10, atol=0.0), k
