@@ -28,9 +28,15 @@ with dL_x/dD = gD + g_O . dO/dD and dL_x/dp = g_O . dO/dp.  G and O are
 differenced as vectors and contracted afterwards, so each quotient's rounding
 is relative to its own output rather than to the whole loss.
 
-Every derivative here is a central finite difference of the oracle's own
-functions, so this gradient shares no derivative formula with the CUDA
-adjoint.  Differences use the fourth-order central stencil
+Every derivative here but one is a central finite difference of the oracle's
+own functions.  The exception is the scale factors: at fixed D the matter state
+does not move with them, and every rate in Eq. implicitMomentsNodal is linear in
+its own factor, so Q_D = (D* + dtau eta)/(1 + dtau chi) and the first-moment
+map I*/(1 + dtau kappa) are ratios of affine functions of each s_k, whose
+derivatives are written out (scale_partials).  A difference quotient loses the
+small derivatives of weakly coupled species (the heavy flavours' absorption) to
+the rounding of Q_D, and at optically thick nodes the adjoint multiplies exactly
+those entries by the large lambda of the number-conserving mode.  Differences use the fourth-order central stencil
 f' = (8 (f(h) - f(-h)) - (f(2h) - f(-2h))) / (12 h).  Steps in D and D* start
 at rel times the entry's natural scale s_j: the change of D_j that moves the
 matter state by O(1) relative, s_j = min(1, rho eps / (MeV W3_j),
@@ -51,7 +57,7 @@ import numpy as np
 from . import eos
 from .constants import C_LIGHT, lepton_numbers
 from .opacities import compute_opacities
-from .solver import moment_map, matter_map, neutrino_energy_number
+from .solver import moment_map, matter_map, neutrino_energy_number, compute_rates
 
 
 def _matter(grid, tables, params, rho, p, D):
@@ -83,6 +89,35 @@ def _outputs(grid, tables, params, rho, p, D, state=None):
     Ms[:, :, 1:] = I_star
     Q = moment_map(M, Ms, op, grid.W2, C_LIGHT * dt)
     return D - Q[:, :, 0], y[1], y[0], T, Q[:, :, 1:]
+
+
+def scale_partials(grid, tables, params, rho, p, D, state):
+    """(dG/ds, dH/ds) at moments D for the four scale factors (EmAb, Iso, NES, Pair), shapes
+    (4, ns, ne) and (4, ns, ne, 3), in closed form.  With unit-factor rates (eta_k, chi_k) of each
+    process at D and the matter state y of `state`:
+        eta = s_0 chi_EmAb D^Eq + s_2 eta_NES + s_3 eta_Pair,  chi = s_0 chi_EmAb + s_2 chi_NES + s_3 chi_Pair,
+        kappa = chi + s_1 sigma_Iso,
+        dQ_D/ds_k = dtau (d eta/ds_k - Q_D d chi/ds_k) / (1 + dtau chi),
+        dH/ds_k = -I* dtau (d kappa/ds_k) / (1 + dtau kappa)^2,
+    and G = D - Q_D."""
+    D_star, I_star, _, _, scale, dt = p
+    _, T, _ = state
+    y = state[0]
+    dtau = C_LIGHT * dt
+    unit = compute_opacities(grid, tables, rho, T, y[1], np.ones(4), params.proc_mask, params.dmin, params.dmax)
+    eta_n, chi_n, eta_p, chi_p = compute_rates(D, unit, grid.W2)
+    ab, sg = unit["chi_ab"], unit["sig"]
+    zero = np.zeros_like(D)
+    deta = [ab * unit["deq"], zero, eta_n, eta_p]
+    dchi = [ab, zero, chi_n, chi_p]
+    dkap = [ab, sg, chi_n, chi_p]
+    eta = sum(scale[k] * deta[k] for k in range(4))
+    chi = sum(scale[k] * dchi[k] for k in range(4))
+    kappa = chi + scale[1] * sg
+    QD = (D_star + dtau * eta) / (1.0 + dtau * chi)
+    dG = np.stack([-dtau * (deta[k] - QD * dchi[k]) / (1.0 + dtau * chi) for k in range(4)])
+    dH = np.stack([-I_star * (dtau * dkap[k] / (1.0 + dtau * kappa) ** 2)[..., None] for k in range(4)])
+    return dG, dH
 
 
 def _stencil(f, h):
@@ -220,8 +255,11 @@ def gradient(grid, tables, params, rho, T_star, Ye_star, D_star, I_star, dt, sca
     out["Ye"], amag["Ye"] = dL_dp(set_entry(2, None), rel * abs(p0[2]))
     out["T"], amag["T"] = dL_dp(set_entry(3, None), rel * abs(p0[3]))
     out["scale"], amag["scale"] = np.empty(4), np.empty(4)
+    dGs, dHs = scale_partials(grid, tables, params, rho, p0, D, state)
     for k in range(4):
-        out["scale"][k], amag["scale"][k] = dL_dp(set_entry(4, k), 1e-3 * max(abs(p0[4][k]), 1e-3), refine=True)
+        t_g, t_h = lam @ dGs[k].ravel(), gH.ravel() @ dHs[k].ravel()
+        out["scale"][k] = t_h - t_g
+        amag["scale"][k] = np.abs(gH.ravel()) @ np.abs(dHs[k].ravel()) + np.abs(lam) @ np.abs(dGs[k].ravel())
     out["cond"] = float(np.linalg.cond(J))
     out["mag"] = amag
     return out

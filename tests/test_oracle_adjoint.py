@@ -92,3 +92,36 @@ def test_gradient_without_first_moment_cotangent_ignores_I_star(grid_tiny):
                             i["dt"][0], i["scale"][0], r["D"], gD=c.gD, gYe=c.gYe, geps=c.geps)
     assert np.all(grad["I_star"] == 0.0)
     assert grad["scale"][1] == 0.0   # isoenergetic scattering enters only H
+
+
+@pytest.mark.parametrize("n,frozen", [(0, 0), (1, 1)])
+def test_scale_partials_closed_form_match_differences(grid_tiny, n, frozen):
+    """The closed-form derivatives of G = D - Q_D and of H with respect to the four scale factors,
+    against fourth-order central differences of the oracle's own map at the converged D (each rate is
+    linear in its factor, so the map is smooth in s_k on the scale of s_k itself)."""
+    c = _Case(grid_tiny, n, frozen, seed=5)
+    i = c.inp
+    _, r = c.loss()
+    p0 = (i["D"][n], i["I"][n], float(i["Ye"][n]), float(i["T"][n]), np.array(i["scale"][n], dtype=float),
+          float(i["dt"][n]))
+    state = adjoint._matter(c.g, c.t, c.params, i["rho"][n], p0, r["D"])
+    dG, dH = adjoint.scale_partials(c.g, c.t, c.params, i["rho"][n], p0, r["D"], state)
+    for k in range(4):
+        def f(t):
+            sc = p0[4].copy()
+            sc[k] += t
+            p = p0[:4] + (sc, p0[5])
+            st = adjoint._matter(c.g, c.t, c.params, i["rho"][n], p, r["D"])
+            G, _, _, _, H = adjoint._outputs(c.g, c.t, c.params, i["rho"][n], p, r["D"], st)
+            return G, H
+        h = 1e-3 * max(p0[4][k], 1e-3)
+        (Gp, Hp), (Gm, Hm), (Gp2, Hp2), (Gm2, Hm2) = f(h), f(-h), f(2 * h), f(-2 * h)
+        fdG = (8 * (Gp - Gm) - (Gp2 - Gm2)) / (12 * h)
+        fdH = (8 * (Hp - Hm) - (Hp2 - Hm2)) / (12 * h)
+        # per species: the difference quotient resolves entries down to ~1e-9 of the species' largest
+        refG = np.max(np.abs(dG[k]), axis=1, keepdims=True) + 1e-300
+        refH = np.max(np.abs(dH[k]), axis=(1, 2), keepdims=True)[..., 0] + 1e-300
+        assert np.all(np.abs(dG[k] - fdG) <= 1e-7 * refG + 1e-9 * np.max(refG)), (k, np.max(np.abs(dG[k] - fdG) / refG))
+        assert np.all(np.abs(dH[k] - fdH) <= 1e-7 * refH[..., None] + 1e-9 * np.max(refH)), k
+    # Iso does not enter Q_D; EmAb, NES and pair do
+    assert np.all(dG[1] == 0.0) and np.any(dG[0] != 0.0) and np.any(dG[2] != 0.0) and np.any(dG[3] != 0.0)
