@@ -58,13 +58,15 @@ namespace {
 
 struct AdjNode {
     double rho, dtau, T, Tp;
+    double Tq[4], yq[4][2];  // the four perturbed matter states of B's differences and their temperatures
     double sc[4];
     double unit[4];
     double ystar[2], y[2], yp[2], h[2];
     double deps_dT_star, deps_dYe_star;
     double g_y[2];           // cotangent of y = (eps, Ye): direct, through T_out and through kappa
     double blk_out[8];
-    double pmax;
+    double pmax, ip;         // |pivot| of the current column and its reciprocal
+    double dinv[128];        // reciprocals of the eliminated diagonal (2 ne <= 128)
     OpacState op;
     int piv;
     int status, bad;
@@ -181,7 +183,11 @@ __global__ void __launch_bounds__(MAXT, MINB) adjoint_kernel(const AdjointArgs a
             nd->status |= NMC_NONFINITE;   // non-finite converged moments
             nd->bad = 1;
         }
-        if (tid == 0 && !nd->bad) {
+        if (tid < 32 && !nd->bad) {
+            // Warp 0: the matter state y = q(D) and the five EoS temperature solves, at y (lane 0) and at
+            // the four states of B's central differences (lanes 1..4: eps + h, eps - h, Ye + h, Ye - h),
+            // side by side: each solve is a chain of dependent FP64 steps, so five lanes cost one.
+            const int ln = tid;
             const double rho = nd->rho;
             double y0, y1;
             if (frozen) { y0 = nd->ystar[0]; y1 = nd->ystar[1]; }
@@ -189,23 +195,38 @@ __global__ void __launch_bounds__(MAXT, MINB) adjoint_kernel(const AdjointArgs a
                 y0 = nd->ystar[0] - (nd->blk_out[2] - nd->blk_out[0]) * kMeVErg / rho;
                 y1 = nd->ystar[1] - kMB * (nd->blk_out[3] - nd->blk_out[1]) / rho;
             }
-            nd->y[0] = y0;
-            nd->y[1] = y1;
+            const double h0 = a.fd_rel * fabs(y0), h1 = a.fd_rel * fabs(y1);
+            double yy0 = y0, yy1 = y1;
+            if (ln >= 1 && ln <= 4) {
+                const double d = (ln & 1) ? 1.0 : -1.0;
+                if (ln <= 2) yy0 += d * h0; else yy1 += d * h1;
+            }
             const double Tg = a.T_out ? a.T_out[n] : a.T[n];
-            bool ok;
-            const double T = eos_temperature(rho, y0, y1, Tg, &ok);
-            if (!ok) { nd->status |= NMC_EOS_FAIL; nd->bad = 1; }
-            nd->T = T;
-            // chain rule through T_out = T(eps, Ye)
-            double e, de;
-            eos_eps(rho, T, y1, &e, &de);
-            const double gT = a.gT ? a.gT[n] : 0.0;
-            const double ge = a.geps ? a.geps[n] : 0.0, gy = a.gYe ? a.gYe[n] : 0.0;
-            nd->g_y[0] = ge + gT / de;
-            nd->g_y[1] = gy - gT * eos_deps_dye(rho, T, y1) / de;
-            nd->h[0] = a.fd_rel * fabs(y0);
-            nd->h[1] = a.fd_rel * fabs(y1);
-            if (!(isfinite(nd->g_y[0]) && isfinite(nd->g_y[1]))) { nd->status |= NMC_NONFINITE; nd->bad = 1; }
+            bool ok = true;
+            double Tk = Tg;
+            if (ln < 5) Tk = eos_temperature(rho, yy0, yy1, Tg, &ok);
+            const bool fail = __ballot_sync(kFull, ln < 5 && !ok) != 0u;
+            if (ln >= 1 && ln <= 4) {
+                nd->Tq[ln - 1] = Tk;
+                nd->yq[ln - 1][0] = yy0;
+                nd->yq[ln - 1][1] = yy1;
+            }
+            if (ln == 0) {
+                nd->y[0] = y0;
+                nd->y[1] = y1;
+                if (fail) { nd->status |= NMC_EOS_FAIL; nd->bad = 1; }
+                nd->T = Tk;
+                // chain rule through T_out = T(eps, Ye)
+                double e, de;
+                eos_eps(rho, Tk, y1, &e, &de);
+                const double gT = a.gT ? a.gT[n] : 0.0;
+                const double ge = a.geps ? a.geps[n] : 0.0, gy = a.gYe ? a.gYe[n] : 0.0;
+                nd->g_y[0] = ge + gT / de;
+                nd->g_y[1] = gy - gT * eos_deps_dye(rho, Tk, y1) / de;
+                nd->h[0] = h0;
+                nd->h[1] = h1;
+                if (!(isfinite(nd->g_y[0]) && isfinite(nd->g_y[1]))) { nd->status |= NMC_NONFINITE; nd->bad = 1; }
+            }
         }
         __syncthreads();
         if (!nd->bad) {
@@ -218,19 +239,10 @@ __global__ void __launch_bounds__(MAXT, MINB) adjoint_kernel(const AdjointArgs a
             double Qp[4] = {0.0, 0.0, 0.0, 0.0}, Kp[4] = {0.0, 0.0, 0.0, 0.0};
             for (int pass = 0; pass < 5; ++pass) {
                 // passes 0..3: (eps + h, eps - h, Ye + h, Ye - h); pass 4: unperturbed
-                if (tid == 0) {
-                    double y0 = nd->y[0], y1 = nd->y[1];
-                    if (pass < 4) {
-                        const double d = (pass & 1) ? -1.0 : 1.0;
-                        if (pass < 2) y0 += d * nd->h[0]; else y1 += d * nd->h[1];
-                        bool ok;
-                        nd->Tp = eos_temperature(nd->rho, y0, y1, nd->T, &ok);
-                        if (!ok) { nd->status |= NMC_EOS_FAIL; nd->bad = 1; }
-                    } else {
-                        nd->Tp = nd->T;
-                    }
-                    nd->yp[0] = y0;
-                    nd->yp[1] = y1;
+                if (tid == 0) {   // the pass's state, solved above
+                    nd->Tp = pass < 4 ? nd->Tq[pass] : nd->T;
+                    nd->yp[0] = pass < 4 ? nd->yq[pass][0] : nd->y[0];
+                    nd->yp[1] = pass < 4 ? nd->yq[pass][1] : nd->y[1];
                 }
                 __syncthreads();
                 if (nd->bad) break;
@@ -339,7 +351,12 @@ __global__ void __launch_bounds__(MAXT, MINB) adjoint_kernel(const AdjointArgs a
                                 const int oi = __shfl_xor_sync(kFull, bi, off);
                                 if (ob2 > best || (ob2 == best && oi < bi)) { best = ob2; bi = oi; }
                             }
-                            if (lane == 0) { nd->piv = bi; nd->pmax = best; }
+                            if (lane == 0) {
+                                nd->piv = bi;
+                                nd->pmax = best;
+                                // one division per column, shared by every row update below
+                                nd->ip = 1.0 / Mt[bi * LDM + c];
+                            }
                         }
                         __syncthreads();
                         const int piv = nd->piv;
@@ -355,7 +372,7 @@ __global__ void __launch_bounds__(MAXT, MINB) adjoint_kernel(const AdjointArgs a
                             }
                             __syncthreads();
                         }
-                        const double ip = 1.0 / Mt[c * LDM + c];
+                        const double ip = nd->ip;
                         for (int r = c + 1 + warp; r < N2; r += nwarps) {
                             const double l = Mt[r * LDM + c] * ip;
                             for (int j = c + 1 + lane; j < N2 + 3; j += 32) Mt[r * LDM + j] -= l * Mt[c * LDM + j];
@@ -364,11 +381,15 @@ __global__ void __launch_bounds__(MAXT, MINB) adjoint_kernel(const AdjointArgs a
                     }
                     __syncthreads();
                     if (nd->bad) break;
-                    // back substitution, one warp per right-hand side
+                    // reciprocals of the diagonal, one lane each, then back substitution, one warp per
+                    // right-hand side
+                    for (int i = tid; i < N2; i += blockDim.x)
+                        if (NMC_IN_BOUNDS(g.dbg, i, 128, kDbgHistory)) nd->dinv[i] = 1.0 / Mt[i * LDM + i];
+                    __syncthreads();
                     for (int k = warp; k < 3; k += nwarps) {
                         const int col = N2 + k;
                         for (int i = N2 - 1; i >= 0; --i) {
-                            const double xi = Mt[i * LDM + col] / Mt[i * LDM + i];
+                            const double xi = Mt[i * LDM + col] * nd->dinv[i];
                             __syncwarp();
                             for (int r = lane; r < i; r += 32) Mt[r * LDM + col] -= Mt[r * LDM + i] * xi;
                             if (lane == 0) Mt[i * LDM + col] = xi;
@@ -473,6 +494,8 @@ size_t adjoint_smem_bytes(const nmc_ctx* ctx, AdjointArgs* a) {
 template <int MAXT, int MINB>
 static int launch_adj_impl(nmc_ctx* ctx, AdjointArgs& a, cudaStream_t stream) {
     auto kern = adjoint_kernel<MAXT, MINB>;
+    if (2 * ctx->ne > 128)   // the reciprocal diagonal of a pair system holds 2 ne <= 128 entries
+        return set_error(ctx, NMC_EUNSUPPORTED, "collision_adjoint supports at most 64 energies");
     const size_t smem = adjoint_smem_bytes(ctx, &a);
     if ((int)smem > ctx->max_smem_optin)
         return set_error(ctx, NMC_EUNSUPPORTED, "shared-memory footprint of the adjoint kernel exceeds the per-block limit");

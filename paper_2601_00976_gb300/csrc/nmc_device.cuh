@@ -458,16 +458,20 @@ struct OpacBufs {
 // The warp of thread `lead` (lane 0 of its warp) does the scalar part; `lead`
 // ORs NMC_TABLE_CLAMP into *status when a lookup leaves a table.
 // Ends with the block synchronised.
-template <typename R>
-__device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const nmc_params& P, double rho,
-                                  double T, double Ye, double dtau, const double* sc, const OpacBufs<R>& b,
-                                  OpacState* os, int* status, R& chiab, R& sig, R& deq, R& deqc, int lead = 0) {
+//
+// BPT bins per thread: species s is served by a group of GS = nep / BPT threads,
+// thread (s, l) owning the bins q = l + k GS, k < BPT (BPT = 1: thread (s, q)).
+// The per-bin results come back in arrays of BPT entries.
+template <typename R, int BPT>
+__device__ void compute_opacities_b(const DevGrid& g, const DevTables& tb, const nmc_params& P, double rho,
+                                    double T, double Ye, double dtau, const double* sc, const OpacBufs<R>& b,
+                                    OpacState* os, int* status, R (&chiab)[BPT], R (&sig)[BPT], R (&deq)[BPT],
+                                    R (&deqc)[BPT], int lead = 0) {
     constexpr bool kMixed = sizeof(R) == 4;
     const int NS = g.ns, NE = g.ne, NEP = g.nep, LD = g.ld;
+    const int GS = NEP / BPT;
     const int tid = threadIdx.x;
-    const int s = tid / NEP, q = tid - s * NEP;
-    const bool act = (s < NS) && (q < NE);
-    const int sq = s * NEP + q;
+    const int s = tid / GS, q = tid - s * GS;   // q: the group lane l (the bin itself when BPT = 1)
     const bool nes_on = (P.proc_mask & NMC_PROC_NES) != 0;
     const bool pair_on = (P.proc_mask & NMC_PROC_PAIR) != 0;
     R* fq = b.phi;
@@ -531,7 +535,7 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         if (s < NS) {
             const R mu = (R)os->mu[s], Tinv = (R)os->tinv;
             const float muh = os->mu_h[s], mul = os->mu_l[s], tih = os->tinv_h, til = os->tinv_l;
-            for (int i = q; i < nqp; i += NEP) {
+            for (int i = q; i < nqp; i += GS) {
                 if (!NMC_IN_BOUNDS(g.dbg, (long long)((kMixed ? NS : 0) + s) * nqp + i, (long long)(kMixed ? 2 : 1) * NS * nqp,
                                    kDbgSmemFd))
                     continue;
@@ -559,11 +563,12 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         }
         __syncthreads();
         // eps^2-weighted projection and bound-enforcing limiter per (species, element)
-        if (s < NS && q < g.n_elem &&
-            NMC_IN_BOUNDS(g.dbg, ((long long)q * g.nq + g.nq - 1) * kProjQuad + kProjQuad - 1,
-                          (long long)g.n_elem * g.nq * kProjQuad, kDbgProj) &&
-            NMC_IN_BOUNDS(g.dbg, (long long)s * NEP + q * g.nq + g.nq - 1, (long long)NS * NEP, kDbgSmemVec)) {
-            const int e = q, nq = g.nq;
+        for (int e = q; s < NS && e < g.n_elem; e += GS) {
+            if (!NMC_IN_BOUNDS(g.dbg, ((long long)e * g.nq + g.nq - 1) * kProjQuad + kProjQuad - 1,
+                               (long long)g.n_elem * g.nq * kProjQuad, kDbgProj) ||
+                !NMC_IN_BOUNDS(g.dbg, (long long)s * NEP + e * g.nq + g.nq - 1, (long long)NS * NEP, kDbgSmemVec))
+                continue;
+            const int nq = g.nq;
             const R* f = fq + s * nqp + e * kProjQuad;
             const R* fc = fq + (NS + s) * nqp + e * kProjQuad;
             R avg = 0, avgc = 0, coef[kMaxNq] = {0, 0, 0}, coefc[kMaxNq] = {0, 0, 0};
@@ -611,14 +616,17 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         __syncthreads();
     }
     // EmAb / Iso: trilinear in (log10 rho, log10 T, Ye) on ln values, times dtau
-    if (act) {
-        deq = b.vDeq[sq];
-        const R dc = kMixed ? b.vDeqc[sq] : (R)1 - deq;
-        deqc = dc;
-        b.vA[sq] = deq / dc;
-        b.vAi[sq] = dc / deq;
+#pragma unroll
+    for (int k = 0; k < BPT; ++k) {
+        const int qb = q + k * GS, sq = s * NEP + qb;
+        if (!(s < NS && qb < NE)) continue;
+        deq[k] = b.vDeq[sq];
+        const R dc = kMixed ? b.vDeqc[sq] : (R)1 - deq[k];
+        deqc[k] = dc;
+        b.vA[sq] = deq[k] / dc;
+        b.vAi[sq] = dc / deq[k];
         const int nr = tb.rho.n, nt = tb.t.n, ny = tb.ye.n;
-        const long long base = ((((long long)s * ny + os->iy) * nt + os->it) * nr + os->ir) * NE + q;
+        const long long base = ((((long long)s * ny + os->iy) * nt + os->it) * nr + os->ir) * NE + qb;
         const long long dR = NE, dT = (long long)nr * NE, dY = (long long)nt * nr * NE;
         const bool tab_ok = NMC_IN_BOUNDS(g.dbg, base, tb.n_op, kDbgEmabIso) &&
                             NMC_IN_BOUNDS(g.dbg, base + dR + dT + dY, tb.n_op, kDbgEmabIso);
@@ -643,8 +651,8 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         li += li0;
         const R pe = kMixed ? (R)os->pre_f[0] : (R)os->pre[0];
         const R pi = kMixed ? (R)os->pre_f[1] : (R)os->pre[1];
-        chiab = (P.proc_mask & NMC_PROC_EMAB) ? pe * r_exp(le) : (R)0;
-        sig = (P.proc_mask & NMC_PROC_ISO) ? pi * r_exp(li) : (R)0;
+        chiab[k] = (P.proc_mask & NMC_PROC_EMAB) ? pe * r_exp(le) : (R)0;
+        sig[k] = (P.proc_mask & NMC_PROC_ISO) ? pi * r_exp(li) : (R)0;
     }
     // NES and pair kernels: bilinear in (log10 T, eta_e), times dtau 4 pi / (hc)^3
     if (nes_on || pair_on) {
@@ -663,7 +671,7 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                 // lower triangle incl. diagonal, entries enumerated row by row so that every lane of the
                 // species group has one (a row loop with q <= r leaves half the lanes idle)
                 const int ntri = NE * (NE + 1) / 2;
-                for (int idx = q; idx < ntri; idx += NEP) {
+                for (int idx = q; idx < ntri; idx += GS) {
                     int r = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
                     while (r * (r + 1) / 2 > idx) --r;
                     while ((r + 1) * (r + 2) / 2 <= idx) ++r;
@@ -683,7 +691,7 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                 const R c = kMixed ? (R)os->pre_f[3] : (R)os->pre[3];
                 const long long off = (((long long)pr * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
                 R* A0 = AN + pr * NE * LD;
-                for (int idx = (s & 1) * NEP + q; idx < NE * NE; idx += 2 * NEP) {
+                for (int idx = (s & 1) * GS + q; idx < NE * NE; idx += 2 * GS) {
                     const int r = idx / NE, cc = idx - r * NE;
                     const long long o = off + idx;
                     if (!NMC_IN_BOUNDS(g.dbg, o + sT + sE, tb.n_pair, kDbgPairTable) ||
@@ -710,7 +718,7 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                 const R* va = b.vA + s * NEP;
                 const R* vai = b.vAi + s * NEP;
                 const int nup = NE * (NE - 1) / 2;   // strictly upper entries, column by column
-                for (int idx = q; idx < nup; idx += NEP) {
+                for (int idx = q; idx < nup; idx += GS) {
                     int cc = (int)((sqrtf(8.0f * idx + 1.0f) + 1.0f) * 0.5f);
                     while (cc * (cc - 1) / 2 > idx) --cc;
                     while ((cc + 1) * cc / 2 <= idx) ++cc;
@@ -727,6 +735,20 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
         if (lin) upper(b.phi1);
     }
     __syncthreads();
+}
+
+// ComputeOpacities with one bin per thread: thread (s, q) = s * nep + q.
+template <typename R>
+__device__ __forceinline__ void compute_opacities(const DevGrid& g, const DevTables& tb, const nmc_params& P,
+                                                  double rho, double T, double Ye, double dtau, const double* sc,
+                                                  const OpacBufs<R>& b, OpacState* os, int* status, R& chiab, R& sig,
+                                                  R& deq, R& deqc, int lead = 0) {
+    R c[1] = {chiab}, si[1] = {sig}, d[1] = {deq}, dc[1] = {deqc};
+    compute_opacities_b<R, 1>(g, tb, P, rho, T, Ye, dtau, sc, b, os, status, c, si, d, dc, lead);
+    chiab = c[0];
+    sig = si[0];
+    deq = d[0];
+    deqc = dc[0];
 }
 
 }  // namespace nmc

@@ -75,6 +75,7 @@ int autotune_fused(nmc_ctx* ctx, const SolveArgs& a, cudaStream_t stream, int32_
     } else {
         for (int pct : pcts) cand.push_back(FusedVariant{1, pct});
     }
+
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);

@@ -24,11 +24,12 @@ sys.path.insert(0, sys.argv[1]); sys.path.insert(0, sys.argv[1] + "/tests")
 from paper_2601_00976_gb300 import nmc, synthetic
 from gpu_helpers import make_case, to_device
 res = {"lib": nmc.LIB_PATH}
+TIGHT = dict(tol_inner=1e-13, tol_outer=1e-13, max_inner=2000)
 for n_elem, de1, kind in ((16, 1.875, "profile"), (32, 1.0, "perturbed")):
     edges, g, tables, inp = make_case(n_elem, de1, 2, 4, kind, 96, seed=7)
     ctx = nmc.Context(edges, 2, 4, tables)
     t = to_device(inp)
-    for name, kw in (("fp64", {}), ("mixed", dict(precision=nmc.MIXED)), ("plain", dict(mode=nmc.MODE_PLAIN))):
+    for name, kw in (("fp64", TIGHT), ("mixed", dict(precision=nmc.MIXED)), ("plain", dict(mode=nmc.MODE_PLAIN, **TIGHT))):
         o = ctx.collision_solve(nmc.default_params(**kw), t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
         torch.cuda.synchronize()
         res[f"{n_elem}_{name}_J"] = o["J"].cpu().numpy().ravel()[::37].tolist()
@@ -38,9 +39,10 @@ for n_elem, de1, kind in ((16, 1.875, "profile"), (32, 1.0, "perturbed")):
         res[f"{n_elem}_interp_{int(mixed)}"] = v.cpu().numpy().tolist()
     if n_elem == 16:
         vel = torch.tensor(synthetic.make_velocities("profile", 96, seed=8), device="cuda")
-        ov = ctx.collision_solve_v(nmc.default_params(), t["rho"], t["T"], t["Ye"], vel, t["D"], t["I"], t["dt"], t["scale"])
-        fw = ctx.collision_solve(nmc.default_params(), t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
-        ga = ctx.collision_adjoint(nmc.default_params(), t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"],
+        ov = ctx.collision_solve_v(nmc.default_params(**TIGHT), t["rho"], t["T"], t["Ye"], vel, t["D"], t["I"], t["dt"],
+                                   t["scale"])
+        fw = ctx.collision_solve(nmc.default_params(**TIGHT), t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"])
+        ga = ctx.collision_adjoint(nmc.default_params(**TIGHT), t["rho"], t["T"], t["Ye"], t["D"], t["I"], t["dt"], t["scale"],
                                    fw["J"], fw["T"], gJ=torch.ones_like(t["D"]))
         c2 = ctx.conserved_to_primitive(t["D"], t["I"], vel)
         torch.cuda.synchronize()
@@ -75,5 +77,11 @@ def test_debug_build_checks_stay_clear_and_match_release():
         a, b = np.asarray(dbg[k]), np.asarray(v)
         if k.endswith("status"):
             assert np.array_equal(a, b), k
-        else:   # the checks add branches, not arithmetic; compilation may still reorder an FMA
-            assert np.allclose(a, b, rtol=1e-9, atol=0), (k, np.max(np.abs(a - b) / np.abs(b)))
+            continue
+        # the checks add branches, not arithmetic, but the two builds are separate compilations whose
+        # rounding differs: FP64 solves run at tol 1e-13 and agree to the parity bar, the mixed one at
+        # its default tolerance to its accuracy target; entries far below the sample's largest are
+        # compared against that largest
+        bar = 1e-5 if "mixed" in k else 1e-10
+        err = np.abs(a - b) / np.maximum(np.abs(b), 1e-4 * np.max(np.abs(b)))
+        assert np.max(err) <= bar, (k, float(np.max(err)))

@@ -52,8 +52,10 @@ def _conservation(g, rho, Ye0, eps0, D0, Ye1, eps1, D1):
     return np.abs(L1 - L0) / np.abs(L0), np.abs(E1 - E0) / np.abs(E0)
 
 
-@pytest.mark.parametrize("kind,n_elem,de1", [("profile", 16, 1.875), ("perturbed", 32, 1.0)])
+@pytest.mark.parametrize("kind,n_elem,de1", [("profile", 16, 1.875), ("perturbed", 32, 1.0), ("perturbed", 24, 1.25)])
 def test_mixed_against_oracle(kind, n_elem, de1):
+    """Grid C (32 energies), Grid F (64) and Grid E (48: the species groups of 64 threads carry 16
+    idle threads each) against the oracle."""
     N = 24
     edges, g, tables, inp = make_case(n_elem, de1, 2, 4, kind, N, seed=21)
     ctx = nmc.Context(edges, 2, 4, tables)
