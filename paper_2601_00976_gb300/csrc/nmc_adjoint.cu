@@ -65,10 +65,13 @@ struct AdjNode {
     double deps_dT_star, deps_dYe_star;
     double g_y[2];           // cotangent of y = (eps, Ye): direct, through T_out and through kappa
     double blk_out[8];
-    double pmax, ip;         // |pivot| of the current column and its reciprocal
     double dinv[128];        // reciprocals of the eliminated diagonal (2 ne <= 128)
+    double cv[2][8];         // per warp: largest |entry| of the next column among its active rows,
+    double cip[2][8];        //   its reciprocal,
+    int ci[2][8];            //   and its row (double-buffered by column parity)
+    int prow[128];           // pivot row of each eliminated column
     OpacState op;
-    int piv;
+
     int status, bad;
 };
 
@@ -337,71 +340,90 @@ __global__ void __launch_bounds__(MAXT, MINB) adjoint_kernel(const AdjointArgs a
                         Mt[c * LDM + N2 + 2] = Cy;
                     }
                     __syncthreads();
-                    // Gaussian elimination with partial pivoting on [P | r Ce Cy]
-                    for (int c = 0; c < N2; ++c) {
-                        if (warp == 0) {
-                            double best = -1.0;
-                            int bi = c;
-                            for (int r = c + lane; r < N2; r += 32) {
-                                const double v = fabs(Mt[r * LDM + c]);
-                                if (v > best) { best = v; bi = r; }
-                            }
-                            for (int off = 16; off > 0; off >>= 1) {
-                                const double ob2 = __shfl_xor_sync(kFull, best, off);
-                                const int oi = __shfl_xor_sync(kFull, bi, off);
-                                if (ob2 > best || (ob2 == best && oi < bi)) { best = ob2; bi = oi; }
-                            }
-                            if (lane == 0) {
-                                nd->piv = bi;
-                                nd->pmax = best;
-                                // one division per column, shared by every row update below
-                                nd->ip = 1.0 / Mt[bi * LDM + c];
-                            }
+                    // Gaussian elimination with partial pivoting on [P | r Ce Cy], rows left in place:
+                    // column c's pivot row is recorded (prow[c]) and leaves the active set, and every warp
+                    // tracks, among the rows it has just updated, the largest |entry| of the next column
+                    // (lane 0 updates that column), so one barrier per column publishes both the updated
+                    // rows and the next pivot's candidates.  Every thread then picks the same pivot.
+                    unsigned long long done0 = 0ull, done1 = 0ull;   // eliminated pivot rows (2 ne <= 128)
+                    auto is_done = [&](int r) {
+                        return ((r < 64 ? done0 >> r : done1 >> (r - 64)) & 1ull) != 0ull;
+                    };
+                    if (lane == 0) {   // column 0's candidates
+                        double nb = -1.0, nip = 0.0;
+                        int ni = 0;
+                        for (int r = warp; r < N2; r += nwarps) {
+                            const double v = fabs(Mt[r * LDM]);
+                            if (v > nb) { nb = v; ni = r; }
                         }
-                        __syncthreads();
-                        const int piv = nd->piv;
-                        if (!(nd->pmax > 1e-300) || !isfinite(nd->pmax)) {   // singular: same decision in every thread
+                        if (nb > 0.0) nip = 1.0 / Mt[ni * LDM];
+                        nd->cv[0][warp] = nb;
+                        nd->ci[0][warp] = ni;
+                        nd->cip[0][warp] = nip;
+                    }
+                    __syncthreads();
+                    for (int c = 0; c < N2; ++c) {
+                        const int bsel = c & 1;
+                        double best = -1.0, ip = 0.0;
+                        int P = 0;
+                        for (int w = 0; w < nwarps; ++w) {
+                            const double v = nd->cv[bsel][w];
+                            const int i = nd->ci[bsel][w];
+                            if (v > best || (v == best && i < P)) { best = v; P = i; ip = nd->cip[bsel][w]; }
+                        }
+                        if (!(best > 1e-300) || !isfinite(best)) {   // singular: same decision in every thread
                             if (tid == 0) { nd->status |= NMC_NONFINITE; nd->bad = 1; }
                             break;
                         }
-                        if (piv != c) {
-                            for (int j = c + tid; j < N2 + 3; j += blockDim.x) {
-                                const double t = Mt[c * LDM + j];
-                                Mt[c * LDM + j] = Mt[piv * LDM + j];
-                                Mt[piv * LDM + j] = t;
-                            }
-                            __syncthreads();
-                        }
-                        const double ip = nd->ip;
-                        for (int r = c + 1 + warp; r < N2; r += nwarps) {
+                        if (!NMC_IN_BOUNDS(g.dbg, P, N2, kDbgHistory)) break;
+                        if (P < 64) done0 |= 1ull << P; else done1 |= 1ull << (P - 64);
+                        if (tid == 0) nd->prow[c] = P;
+                        double nb = -1.0;
+                        int ni = 0;
+                        for (int r = warp; r < N2; r += nwarps) {
+                            if (is_done(r)) continue;
                             const double l = Mt[r * LDM + c] * ip;
-                            for (int j = c + 1 + lane; j < N2 + 3; j += 32) Mt[r * LDM + j] -= l * Mt[c * LDM + j];
+                            for (int j = c + 1 + lane; j < N2 + 3; j += 32) Mt[r * LDM + j] -= l * Mt[P * LDM + j];
+                            if (lane == 0 && c + 1 < N2) {
+                                const double v = fabs(Mt[r * LDM + c + 1]);
+                                if (v > nb) { nb = v; ni = r; }
+                            }
+                        }
+                        if (lane == 0) {
+                            nd->cv[bsel ^ 1][warp] = nb;
+                            nd->ci[bsel ^ 1][warp] = ni;
+                            nd->cip[bsel ^ 1][warp] = nb > 0.0 ? 1.0 / Mt[ni * LDM + c + 1] : 0.0;
                         }
                         __syncthreads();
                     }
                     __syncthreads();
                     if (nd->bad) break;
-                    // reciprocals of the diagonal, one lane each, then back substitution, one warp per
-                    // right-hand side
+                    // reciprocals of the diagonal of the eliminated (row-permuted) system, then back
+                    // substitution in pivot order, one warp per right-hand side
                     for (int i = tid; i < N2; i += blockDim.x)
-                        if (NMC_IN_BOUNDS(g.dbg, i, 128, kDbgHistory)) nd->dinv[i] = 1.0 / Mt[i * LDM + i];
+                        if (NMC_IN_BOUNDS(g.dbg, i, 128, kDbgHistory)) nd->dinv[i] = 1.0 / Mt[nd->prow[i] * LDM + i];
                     __syncthreads();
                     for (int k = warp; k < 3; k += nwarps) {
                         const int col = N2 + k;
                         for (int i = N2 - 1; i >= 0; --i) {
-                            const double xi = Mt[i * LDM + col] * nd->dinv[i];
+                            const int pi = nd->prow[i];
+                            const double xi = Mt[pi * LDM + col] * nd->dinv[i];
                             __syncwarp();
-                            for (int r = lane; r < i; r += 32) Mt[r * LDM + col] -= Mt[r * LDM + i] * xi;
-                            if (lane == 0) Mt[i * LDM + col] = xi;
+                            for (int r = lane; r < i; r += 32) {
+                                const int pr = nd->prow[r];
+                                Mt[pr * LDM + col] -= Mt[pr * LDM + i] * xi;
+                            }
+                            if (lane == 0) Mt[pi * LDM + col] = xi;
                             __syncwarp();
                         }
                     }
                     __syncthreads();
-                    if (mine) {
+                    if (mine) {   // unknown c sits in its pivot row
                         const int c = (s & 1) * NE + q;
-                        x = Mt[c * LDM + N2 + 0];
-                        ze = Mt[c * LDM + N2 + 1];
-                        zy = Mt[c * LDM + N2 + 2];
+                        const int pc = nd->prow[c];
+                        x = Mt[pc * LDM + N2 + 0];
+                        ze = Mt[pc * LDM + N2 + 1];
+                        zy = Mt[pc * LDM + N2 + 2];
                     }
                     __syncthreads();
                 }

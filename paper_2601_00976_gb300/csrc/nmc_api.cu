@@ -100,6 +100,23 @@ int upload_f32(nmc_ctx* ctx, const double* host, size_t count, double scale, con
     return upload(ctx, tmp.data(), count, dev);
 }
 
+// The ln table [ns][nye][nt][nrho][ne] regrouped for opacity_interp_mixed: for every
+// (rho, E) cell one float4 of its four corners, so that the 16 corner values of a
+// point come in four 16-byte loads.
+int upload_quads(nmc_ctx* ctx, const double* host, int ns, int nye, int nt, int nr, int ne, const float4** dev) {
+    const size_t nrc = (size_t)(nr - 1), nec = (size_t)(ne - 1);
+    std::vector<float4> q((size_t)ns * nye * nt * nrc * nec);
+    size_t k = 0;
+    for (size_t a = 0; a < (size_t)ns * nye * nt; ++a)
+        for (size_t ir = 0; ir < nrc; ++ir)
+            for (size_t e = 0; e < nec; ++e) {
+                const double* r0 = host + (a * nr + ir) * ne + e;
+                const double* r1 = r0 + ne;
+                q[k++] = make_float4((float)r0[0], (float)r1[0], (float)r0[1], (float)r1[1]);
+            }
+    return upload(ctx, q.data(), q.size(), dev);
+}
+
 Axis make_axis(double lo, double hi, int n) {
     Axis a;
     a.lo = lo;
@@ -348,6 +365,9 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
     // FP32 copies for the mixed path; kernel tables prescaled by 4 pi / (hc)^3
     if (rc == NMC_OK) rc = upload_f32(ctx, tb->emab, n_op, 1.0, &t.emab_f);
     if (rc == NMC_OK) rc = upload_f32(ctx, tb->iso, n_op, 1.0, &t.iso_f);
+    if (rc == NMC_OK) rc = upload_quads(ctx, tb->emab, ns, tb->n_ye, tb->n_t, tb->n_rho, ne, &t.emab_q);
+    if (rc == NMC_OK) rc = upload_quads(ctx, tb->iso, ns, tb->n_ye, tb->n_t, tb->n_rho, ne, &t.iso_q);
+    t.n_quad = (long long)ns * tb->n_ye * tb->n_t * (tb->n_rho - 1) * (ne - 1);
     if (rc == NMC_OK) rc = upload_f32(ctx, tb->nes, n_nes, kCW, &t.nes_f);
     if (rc == NMC_OK) rc = upload_f32(ctx, tb->pair, n_pair, kCW, &t.pair_f);
     if (rc == NMC_OK) {

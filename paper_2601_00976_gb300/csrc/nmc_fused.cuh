@@ -559,9 +559,28 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         }
                         if (s < NS) vote = species_ok(v, s);
                     } else {
-                        R* out = reinterpret_cast<R*>(nd->sp_out);
-                        species_sum<4, R>(v, red, out, NEP, NS);
-                        for (int sp = 0; sp < NS; ++sp) vote &= species_ok(out + sp * 4, sp);
+                        // a species spans NEP / 32 warps: warp sums by shuffles, then a barrier over that
+                        // species' warps only (named barrier 1 + s; barrier 0 is the block's), after which
+                        // every thread adds its species' partials in the same order and votes for it.  The
+                        // scratch is free here: the lead warp read the Gram partials before the previous
+                        // barrier, and the next ones are written after the vote's.
+                        const int wps = NEP >> 5, lane = tid & 31, w = tid >> 5;
+                        for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) v[c] += __shfl_xor_sync(kFull, v[c], off);
+                        }
+                        R* pv = reinterpret_cast<R*>(red);
+                        if (lane == 0) {
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) pv[w * 4 + c] = v[c];
+                        }
+                        asm volatile("bar.sync %0, %1;" ::"r"(1 + s), "r"(wps * 32) : "memory");
+                        R u[4] = {0, 0, 0, 0};
+                        for (int i = 0; i < wps; ++i) {
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) u[c] += pv[(s * wps + i) * 4 + c];
+                        }
+                        vote = species_ok(u, s);
                     }
                 }
                 const bool conv = __syncthreads_and(vote) != 0;

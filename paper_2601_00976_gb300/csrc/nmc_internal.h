@@ -105,6 +105,11 @@ struct DevTables {
     const float* nes_f;
     const float* pair_f;
     long long n_op, n_nes, n_pair;   // element counts of the EmAb/Iso, NES and pair tables
+    // opacity_interp_mixed: the FP32 ln tables regrouped per (rho, E) cell, one float4
+    // (rho_i E_q, rho_i+1 E_q, rho_i E_q+1, rho_i+1 E_q+1) per [ns][nye][nt][nrho-1][ne-1]
+    const float4* emab_q;
+    const float4* iso_q;
+    long long n_quad;
 };
 
 struct SolveArgs {

@@ -5,12 +5,14 @@
 // energies of the grid) is searched by bisection in ln E; the 16 corner ln
 // values are combined with the tensor-product weights and exponentiated.
 //
-// opacity_interp_mixed: the same interpolation in FP32 on the FP32 copies of
-// the ln tables (the mixed-precision solve's opacities): FP32 logarithms, cell
-// search and weights, the ln value as the first corner plus weighted
-// differences (the corners are ~ -20, whose FP32 sum would round ln chi by
-// ~2e-6 in steps), and an FP32 exp; inputs and outputs stay FP64.  The energy
-// axis is searched in a shared-memory copy of ln eps.
+// opacity_interp_mixed: the same interpolation in FP32 on FP32 copies of the
+// ln tables: FP32 logarithms, cell search and weights, the ln value as the
+// first corner plus weighted differences (the corners are ~ -20, whose FP32
+// sum would round ln chi by ~2e-6 in steps), and an FP32 exp; inputs and
+// outputs stay FP64.  The energy axis is searched in a shared-memory copy of
+// ln eps.  The table copy is regrouped per (rho, E) cell, four corners to a
+// float4, so a point's 16 corner values take four 16-byte loads (four L2
+// sectors) rather than sixteen scattered words.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -90,8 +92,9 @@ __global__ void __launch_bounds__(256) opacity_interp_mixed_kernel(const DevGrid
     const int NE = g.ne;
     for (int q = threadIdx.x; q < NE; q += blockDim.x) lne[q] = (float)g.lneps[q];
     __syncthreads();
-    const float* __restrict__ tab = which == 0 ? tb.emab_f : tb.iso_f;
-    const long long dR = NE, dT = (long long)tb.rho.n * NE, dY = (long long)tb.t.n * tb.rho.n * NE;
+    const float4* __restrict__ tab = which == 0 ? tb.emab_q : tb.iso_q;
+    const long long nrc = tb.rho.n - 1, nec = NE - 1;
+    const long long dT = nrc * nec, dY = (long long)tb.t.n * nrc * nec;
     const long long sp0 = (long long)species * tb.ye.n;
     const float lo_e = lne[0], hi_e = lne[NE - 1];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < p; i += (long long)gridDim.x * blockDim.x) {
@@ -109,24 +112,23 @@ __global__ void __launch_bounds__(256) opacity_interp_mixed_kernel(const DevGrid
             if (lne[mid] <= le) lo = mid; else hi = mid;
         }
         const float te = (le - lne[lo]) / (lne[lo + 1] - lne[lo]);
-        const long long base = (((sp0 + iy) * tb.t.n + it) * tb.rho.n + ir) * NE + lo;
-        if (!NMC_IN_BOUNDS(g.dbg, base, tb.n_op, kDbgEmabIso) ||
-            !NMC_IN_BOUNDS(g.dbg, base + dR + dT + dY + 1, tb.n_op, kDbgEmabIso))
+        // the (rho, E) cell's four corners per load: (T, Ye) corners k = cb + 2 cc
+        const long long base = (((sp0 + iy) * tb.t.n + it) * nrc + ir) * nec + lo;
+        if (!NMC_IN_BOUNDS(g.dbg, base, tb.n_quad, kDbgEmabIso) ||
+            !NMC_IN_BOUNDS(g.dbg, base + dT + dY, tb.n_quad, kDbgEmabIso))
             continue;
-        float c[16];
+        float4 c[4];
 #pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) {
-            const long long o = base + (c8 & 1) * dR + ((c8 >> 1) & 1) * dT + (c8 >> 2) * dY;
-            c[2 * c8] = __ldg(tab + o);
-            c[2 * c8 + 1] = __ldg(tab + o + 1);
-        }
-        const float c0 = c[0];
+        for (int k = 0; k < 4; ++k) c[k] = __ldg(tab + base + (k & 1) * dT + (k >> 1) * dY);
+        const float c0 = c[0].x;
         float v = 0.0f;
 #pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) {
-            const int ca = c8 & 1, cb = (c8 >> 1) & 1, cc = c8 >> 2;
-            const float w = (ca ? tr : 1.0f - tr) * (cb ? tt : 1.0f - tt) * (cc ? ty : 1.0f - ty);
-            v = fmaf(w, fmaf(te, c[2 * c8 + 1] - c[2 * c8], c[2 * c8] - c0), v);
+        for (int k = 0; k < 4; ++k) {
+            const float wk = ((k & 1) ? tt : 1.0f - tt) * ((k >> 1) ? ty : 1.0f - ty);
+            // rho_i and rho_i+1, each linear in ln E between the two energy nodes
+            const float a0 = fmaf(te, c[k].z - c[k].x, c[k].x - c0);
+            const float a1 = fmaf(te, c[k].w - c[k].y, c[k].y - c0);
+            v = fmaf(wk, fmaf(tr, a1 - a0, a0), v);
         }
         out[i] = (double)expf(c0 + v);
     }
