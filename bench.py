@@ -75,9 +75,9 @@ WORKLOAD = ("perturbed collapse profile (+-10% seeded perturbations of rho, T, Y
 # dram__bytes_write.sum); traffic grows with the node count.  None where the kernel has changed since its
 # counters were taken.
 TRAFFIC_PER_NODE = {"fused_kernel<double>": None, "fused_kernel<float>": None,
-                    "adjoint_kernel": 875135232 / 65536, "velocity_kernel": 524328704 / 65536,
-                    "c2p_kernel": 530723584 / 65536, "opacity_interp_kernel": None,
-                    "opacity_interp_mixed_kernel": None}
+                    "adjoint_kernel": 203109376 / 16384, "velocity_kernel": 524328704 / 65536,
+                    "c2p_kernel": 530723584 / 65536, "opacity_interp_kernel": 159e6 / (1 << 22),
+                    "opacity_interp_mixed_kernel": 162e6 / (1 << 22)}
 
 
 def _traffic(kernel, n):

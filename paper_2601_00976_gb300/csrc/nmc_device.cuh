@@ -458,20 +458,23 @@ struct OpacBufs {
 // The warp of thread `lead` (lane 0 of its warp) does the scalar part; `lead`
 // ORs NMC_TABLE_CLAMP into *status when a lookup leaves a table.
 // Ends with the block synchronised.
-//
-// BPT bins per thread: species s is served by a group of GS = nep / BPT threads,
-// thread (s, l) owning the bins q = l + k GS, k < BPT (BPT = 1: thread (s, q)).
-// The per-bin results come back in arrays of BPT entries.
-template <typename R, int BPT>
-__device__ void compute_opacities_b(const DevGrid& g, const DevTables& tb, const nmc_params& P, double rho,
-                                    double T, double Ye, double dtau, const double* sc, const OpacBufs<R>& b,
-                                    OpacState* os, int* status, R (&chiab)[BPT], R (&sig)[BPT], R (&deq)[BPT],
-                                    R (&deqc)[BPT], int lead = 0) {
+// Thread (s, q) = s * nep + q owns species s at energy node q and gets its
+// bin's chi_EmAb, sigma_Iso, D^Eq and 1 - D^Eq back.
+// ComputeOpacities' load batches: Fermi--Dirac points per thread, and kernel-table entries per
+// thread in the NES/pair fill (four corners each; fewer in FP64, whose values take two registers).
+constexpr int kFdBatch = 8;
+constexpr int kFillBatchF32 = 6;
+constexpr int kFillBatchF64 = 4;
+
+template <typename R>
+__device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const nmc_params& P, double rho, double T,
+                                  double Ye, double dtau, const double* sc, const OpacBufs<R>& b, OpacState* os,
+                                  int* status, R& chiab, R& sig, R& deq, R& deqc, int lead = 0) {
     constexpr bool kMixed = sizeof(R) == 4;
     const int NS = g.ns, NE = g.ne, NEP = g.nep, LD = g.ld;
-    const int GS = NEP / BPT;
+    const int GS = NEP;   // threads per species
     const int tid = threadIdx.x;
-    const int s = tid / GS, q = tid - s * GS;   // q: the group lane l (the bin itself when BPT = 1)
+    const int s = tid / GS, q = tid - s * GS;
     const bool nes_on = (P.proc_mask & NMC_PROC_NES) != 0;
     const bool pair_on = (P.proc_mask & NMC_PROC_PAIR) != 0;
     R* fq = b.phi;
@@ -529,102 +532,153 @@ __device__ void compute_opacities_b(const DevGrid& g, const DevTables& tb, const
         }
     }
     __syncthreads();
-    // Fermi--Dirac at the projection quadrature points of every element
+    // Fermi--Dirac at the projection quadrature points of every element.  The table reads of
+    // this function hit L2 at several hundred cycles each, so every stage issues its loads in
+    // straight-line batches (indices clamped into range, the results' stores guarded): one
+    // memory latency per batch instead of one per loop trip.
     {
         const int nqp = g.n_elem * kProjQuad;
         if (s < NS) {
             const R mu = (R)os->mu[s], Tinv = (R)os->tinv;
             const float muh = os->mu_h[s], mul = os->mu_l[s], tih = os->tinv_h, til = os->tinv_l;
-            for (int i = q; i < nqp; i += GS) {
-                if (!NMC_IN_BOUNDS(g.dbg, (long long)((kMixed ? NS : 0) + s) * nqp + i, (long long)(kMixed ? 2 : 1) * NS * nqp,
-                                   kDbgSmemFd))
-                    continue;
-                if (kMixed) {
-                    // f and 1 - f from one exp, each without cancellation.  x = (E - mu)/T reaches
-                    // ~100 in the tail, where rounding x to FP32 would move exp(-|x|) by ~1e-5 in
-                    // steps; x is formed as a double-float, e^-|x| = expf(-|x_hi|) (1 - |x|_lo)
-                    float e1, e2;
-                    const float d0 = two_sum(g.proj_e_f[i], -muh, &e1);
-                    const float dh = two_sum(d0, __fadd_rn(e1, __fsub_rn(g.proj_e_fl[i], mul)), &e2);
-                    const float x0 = __fmul_rn(dh, tih);
-                    float x1 = fmaf(dh, tih, -x0);   // dh tih = x0 + x1 exactly
-                    x1 = fmaf(dh, til, x1);
-                    x1 = fmaf(e2, tih, x1);
-                    const bool pos = x0 > 0.f;
-                    const float xh = fabsf(x0), xl = pos ? x1 : -x1;
-                    const R t = r_exp(-xh) * (1.0f - xl);
-                    const R inv = (R)1 / ((R)1 + t);
-                    fq[s * nqp + i] = pos ? t * inv : inv;
-                    fq[(NS + s) * nqp + i] = pos ? inv : t * inv;
-                } else {
-                    fq[s * nqp + i] = (R)1 / (r_exp(((R)g.proj_e[i] - mu) * Tinv) + (R)1);
+            for (int i0 = q; i0 < nqp; i0 += kFdBatch * GS) {
+                R eh[kFdBatch];
+                float el[kFdBatch];
+#pragma unroll
+                for (int u = 0; u < kFdBatch; ++u) {
+                    const int i = min(i0 + u * GS, nqp - 1);
+                    if constexpr (kMixed) {
+                        eh[u] = __ldg(g.proj_e_f + i);
+                        el[u] = __ldg(g.proj_e_fl + i);
+                    } else {
+                        eh[u] = __ldg(g.proj_e + i);
+                        el[u] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kFdBatch; ++u) {
+                    const int i = i0 + u * GS;
+                    R fv, fcv = 0;
+                    if constexpr (kMixed) {
+                        // f and 1 - f from one exp, each without cancellation.  x = (E - mu)/T reaches
+                        // ~100 in the tail, where rounding x to FP32 would move exp(-|x|) by ~1e-5 in
+                        // steps; x is formed as a double-float, e^-|x| = expf(-|x_hi|) (1 - |x|_lo)
+                        float e1, e2;
+                        const float d0 = two_sum(eh[u], -muh, &e1);
+                        const float dh = two_sum(d0, __fadd_rn(e1, __fsub_rn(el[u], mul)), &e2);
+                        const float x0 = __fmul_rn(dh, tih);
+                        float x1 = fmaf(dh, tih, -x0);   // dh tih = x0 + x1 exactly
+                        x1 = fmaf(dh, til, x1);
+                        x1 = fmaf(e2, tih, x1);
+                        const bool pos = x0 > 0.f;
+                        const float xh = fabsf(x0), xl = pos ? x1 : -x1;
+                        const R t = r_exp(-xh) * (1.0f - xl);
+                        const R inv = (R)1 / ((R)1 + t);
+                        fv = pos ? t * inv : inv;
+                        fcv = pos ? inv : t * inv;
+                    } else {
+                        fv = (R)1 / (r_exp((eh[u] - mu) * Tinv) + (R)1);
+                    }
+                    if (i < nqp && NMC_IN_BOUNDS(g.dbg, (long long)((kMixed ? NS : 0) + s) * nqp + i,
+                                                 (long long)(kMixed ? 2 : 1) * NS * nqp, kDbgSmemFd)) {
+                        fq[s * nqp + i] = fv;
+                        if constexpr (kMixed) fq[(NS + s) * nqp + i] = fcv;
+                    }
                 }
             }
         }
         __syncthreads();
-        // eps^2-weighted projection and bound-enforcing limiter per (species, element)
+        // eps^2-weighted projection and bound-enforcing limiter per (species, element), the sums over
+        // the quadrature points taken in order, their operator weights loaded kProjQuad / 2 points at a
+        // time.  With D^Eq also a = D^Eq / (1 - D^Eq) and 1 / a, which the detailed-balance fill of the
+        // NES kernel reads across the species.
+        constexpr int kHalfQ = kProjQuad / 2;
         for (int e = q; s < NS && e < g.n_elem; e += GS) {
-            if (!NMC_IN_BOUNDS(g.dbg, ((long long)e * g.nq + g.nq - 1) * kProjQuad + kProjQuad - 1,
-                               (long long)g.n_elem * g.nq * kProjQuad, kDbgProj) ||
-                !NMC_IN_BOUNDS(g.dbg, (long long)s * NEP + e * g.nq + g.nq - 1, (long long)NS * NEP, kDbgSmemVec))
-                continue;
             const int nq = g.nq;
+            if (!NMC_IN_BOUNDS(g.dbg, ((long long)e * nq + nq - 1) * kProjQuad + kProjQuad - 1,
+                               (long long)g.n_elem * nq * kProjQuad, kDbgProj) ||
+                !NMC_IN_BOUNDS(g.dbg, (long long)s * NEP + e * nq + nq - 1, (long long)NS * NEP, kDbgSmemVec))
+                continue;
             const R* f = fq + s * nqp + e * kProjQuad;
             const R* fc = fq + (NS + s) * nqp + e * kProjQuad;
             R avg = 0, avgc = 0, coef[kMaxNq] = {0, 0, 0}, coefc[kMaxNq] = {0, 0, 0};
-            for (int gq = 0; gq < kProjQuad; ++gq) {
-                const R pa = kMixed ? (R)g.proj_a_f[e * kProjQuad + gq] : (R)g.proj_a[e * kProjQuad + gq];
-                const R fv = f[gq];
-                avg += pa * fv;
-                R fcv = 0;
-                if (kMixed) { fcv = fc[gq]; avgc += pa * fcv; }
-                for (int pp = 0; pp < nq; ++pp) {
-                    const int o = (e * nq + pp) * kProjQuad + gq;
-                    const R pc = kMixed ? (R)g.proj_c_f[o] : (R)g.proj_c[o];
-                    coef[pp] += pc * fv;
-                    if (kMixed) coefc[pp] += pc * fcv;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                R pa[kHalfQ], pc[kMaxNq][kHalfQ];
+#pragma unroll
+                for (int gq = 0; gq < kHalfQ; ++gq) {
+                    const int qa = e * kProjQuad + h * kHalfQ + gq;
+                    pa[gq] = kMixed ? (R)__ldg(g.proj_a_f + qa) : (R)__ldg(g.proj_a + qa);
+#pragma unroll
+                    for (int pp = 0; pp < kMaxNq; ++pp) {
+                        const int o = (e * nq + min(pp, nq - 1)) * kProjQuad + h * kHalfQ + gq;
+                        pc[pp][gq] = kMixed ? (R)__ldg(g.proj_c_f + o) : (R)__ldg(g.proj_c + o);
+                    }
+                }
+#pragma unroll
+                for (int gq = 0; gq < kHalfQ; ++gq) {
+                    const R fv = f[h * kHalfQ + gq];
+                    avg += pa[gq] * fv;
+                    R fcv = 0;
+                    if (kMixed) { fcv = fc[h * kHalfQ + gq]; avgc += pa[gq] * fcv; }
+#pragma unroll
+                    for (int pp = 0; pp < kMaxNq; ++pp) {
+                        if (pp >= nq) break;
+                        coef[pp] += pc[pp][gq] * fv;
+                        if (kMixed) coefc[pp] += pc[pp][gq] * fcv;
+                    }
                 }
             }
             const R dmin = (R)P.d_min, dmax = (R)P.d_max;
+            // loops over the element's nq <= kMaxNq nodes, unrolled to kMaxNq so that the arrays stay in
+            // registers
             if (avg < dmin || avg > dmax) {
                 const bool lo = avg < dmin;
                 const R cv = lo ? dmin : dmax;
                 const R cvc = lo ? (R)(1.0 - P.d_min) : (R)(1.0 - P.d_max);
-                for (int pp = 0; pp < nq; ++pp) { coef[pp] = cv; coefc[pp] = cvc; }
+#pragma unroll
+                for (int pp = 0; pp < kMaxNq; ++pp) { coef[pp] = cv; coefc[pp] = cvc; }
             } else {
                 R vmin = coef[0], vmax = coef[0];
-                for (int pp = 1; pp < nq; ++pp) { vmin = fmin(vmin, coef[pp]); vmax = fmax(vmax, coef[pp]); }
+#pragma unroll
+                for (int pp = 1; pp < kMaxNq; ++pp)
+                    if (pp < nq) { vmin = fmin(vmin, coef[pp]); vmax = fmax(vmax, coef[pp]); }
+#pragma unroll
                 for (int side = 0; side < 2; ++side) {
                     R v = 0;
-                    for (int pp = 0; pp < nq; ++pp) v += coef[pp] * (R)g.ends[side][pp];
+#pragma unroll
+                    for (int pp = 0; pp < kMaxNq; ++pp)
+                        if (pp < nq) v += coef[pp] * (R)g.ends[side][pp];
                     vmin = fmin(vmin, v);
                     vmax = fmax(vmax, v);
                 }
                 R theta = 1;
                 if (vmin < dmin) theta = fmin(theta, (avg - dmin) / (avg - vmin));
                 if (vmax > dmax) theta = fmin(theta, (dmax - avg) / (vmax - avg));
-                for (int pp = 0; pp < nq; ++pp) {
+#pragma unroll
+                for (int pp = 0; pp < kMaxNq; ++pp) {
                     coef[pp] = avg + theta * (coef[pp] - avg);
                     coefc[pp] = avgc + theta * (coefc[pp] - avgc);
                 }
             }
-            for (int pp = 0; pp < nq; ++pp) {
-                b.vDeq[s * NEP + e * nq + pp] = coef[pp];
-                b.vDeqc[s * NEP + e * nq + pp] = coefc[pp];
+#pragma unroll
+            for (int pp = 0; pp < kMaxNq; ++pp) {
+                if (pp >= nq) break;
+                const int sq = s * NEP + e * nq + pp;
+                const R dc = kMixed ? coefc[pp] : (R)1 - coef[pp];
+                b.vDeq[sq] = coef[pp];
+                b.vDeqc[sq] = coefc[pp];
+                b.vA[sq] = coef[pp] / dc;
+                b.vAi[sq] = dc / coef[pp];
             }
         }
         __syncthreads();
     }
     // EmAb / Iso: trilinear in (log10 rho, log10 T, Ye) on ln values, times dtau
-#pragma unroll
-    for (int k = 0; k < BPT; ++k) {
-        const int qb = q + k * GS, sq = s * NEP + qb;
-        if (!(s < NS && qb < NE)) continue;
-        deq[k] = b.vDeq[sq];
-        const R dc = kMixed ? b.vDeqc[sq] : (R)1 - deq[k];
-        deqc[k] = dc;
-        b.vA[sq] = deq[k] / dc;
-        b.vAi[sq] = dc / deq[k];
+    if (s < NS && q < NE) {
+        const int qb = q, sq = s * NEP + q;
+        deq = b.vDeq[sq];
+        deqc = kMixed ? b.vDeqc[sq] : (R)1 - deq;
         const int nr = tb.rho.n, nt = tb.t.n, ny = tb.ye.n;
         const long long base = ((((long long)s * ny + os->iy) * nt + os->it) * nr + os->ir) * NE + qb;
         const long long dR = NE, dT = (long long)nr * NE, dY = (long long)nt * nr * NE;
@@ -651,8 +705,8 @@ __device__ void compute_opacities_b(const DevGrid& g, const DevTables& tb, const
         li += li0;
         const R pe = kMixed ? (R)os->pre_f[0] : (R)os->pre[0];
         const R pi = kMixed ? (R)os->pre_f[1] : (R)os->pre[1];
-        chiab[k] = (P.proc_mask & NMC_PROC_EMAB) ? pe * r_exp(le) : (R)0;
-        sig[k] = (P.proc_mask & NMC_PROC_ISO) ? pi * r_exp(li) : (R)0;
+        chiab = (P.proc_mask & NMC_PROC_EMAB) ? pe * r_exp(le) : (R)0;
+        sig = (P.proc_mask & NMC_PROC_ISO) ? pi * r_exp(li) : (R)0;
     }
     // NES and pair kernels: bilinear in (log10 T, eta_e), times dtau 4 pi / (hc)^3
     if (nes_on || pair_on) {
@@ -662,93 +716,100 @@ __device__ void compute_opacities_b(const DevGrid& g, const DevTables& tb, const
         const R w01 = ((R)1 - kt) * ke, w11 = kt * ke;
         const long long mat = (long long)NE * NE;
         const long long sE = mat, sT = (long long)tb.eta.n * mat;
-        // lower NES triangle and the pair matrix of one kernel order (Phi_0, or Phi_1 in PH1/AN1)
+        // One kernel order (Phi_0, or Phi_1 into PH1/AN1), as a list of jobs per lane of the species
+        // group, each one table entry (a row pass puts the lanes of a warp on contiguous runs of a row),
+        // taken in straight-line batches whose four-corner loads are all issued before any is combined.
+        //  NES: the tabulated lower triangle (q >= q'), each entry also giving its up-scattering
+        //  mirror by detailed balance, K[c][r] = a_r / a_c K[r][c] for c < r (the a of the species
+        //  were formed with D^Eq).  Job p < NE/2 pairs row p (p + 1 entries, lanes 0..p) with row
+        //  NE-1-p (its NE-1-p off-diagonal entries, lanes p+1..NE-1); job NE/2 takes the diagonals
+        //  of those rows and, for odd NE, the middle row.
+        //  Pair: the whole K_Ann of each particle/antiparticle pair, the particle's group taking the
+        //  even rows and the antiparticle's the odd ones (lane q: column q).
         auto fill = [&](const double* tn, const float* tnf, const double* tp, const float* tpf, R* PH, R* AN) {
-            if (nes_on && s < NS) {
-                const R c = kMixed ? (R)os->pre_f[2] : (R)os->pre[2];
-                const long long off = (((long long)s * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
-                R* P0 = PH + s * NE * LD;
-                // lower triangle incl. diagonal, entries enumerated row by row so that every lane of the
-                // species group has one (a row loop with q <= r leaves half the lanes idle)
-                const int ntri = NE * (NE + 1) / 2;
-                for (int idx = q; idx < ntri; idx += GS) {
-                    int r = (int)((sqrtf(8.0f * idx + 1.0f) - 1.0f) * 0.5f);
-                    while (r * (r + 1) / 2 > idx) --r;
-                    while ((r + 1) * (r + 2) / 2 <= idx) ++r;
-                    const int cc = idx - r * (r + 1) / 2;
-                    const long long o = off + (long long)r * NE + cc;
-                    if (!NMC_IN_BOUNDS(g.dbg, o + sT + sE, tb.n_nes, kDbgNesTable) ||
-                        !NMC_IN_BOUNDS(g.dbg, (long long)s * NE * LD + r * LD + cc, (long long)NS * NE * LD, kDbgSmemNes))
-                        continue;
-                    R v;
-                    if (kMixed) v = w00 * tnf[o] + w10 * tnf[o + sT] + w01 * tnf[o + sE] + w11 * tnf[o + sT + sE];
-                    else v = w00 * tn[o] + w10 * tn[o + sT] + w01 * tn[o + sE] + w11 * tn[o + sT + sE];
-                    P0[r * LD + cc] = c * v;
+            if (s >= NS || q >= NE) return;
+            constexpr int kB = kMixed ? kFillBatchF32 : kFillBatchF64;
+            const int half = NE >> 1, pr = s >> 1;
+            const int n_nes = nes_on ? half + 1 : 0;
+            const int n_pair = pair_on ? (NE - (s & 1) + 1) >> 1 : 0;
+            const int njobs = n_nes + n_pair;
+            const long long off_n = (((long long)s * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
+            const long long off_p = (((long long)pr * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
+            const R c_n = kMixed ? (R)os->pre_f[2] : (R)os->pre[2];
+            const R c_p = kMixed ? (R)os->pre_f[3] : (R)os->pre[3];
+            R* P0 = PH + s * NE * LD;
+            R* A0 = AN + pr * NE * LD;
+            const R* va = b.vA + s * NEP;
+            const R* vai = b.vAi + s * NEP;
+            for (int j0 = 0; j0 < njobs; j0 += kB) {
+                int rr[kB], cl[kB];
+                R t[kB][4];
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int jj = min(j0 + u, njobs - 1);
+                    int r, cc;
+                    const bool isn = jj < n_nes;
+                    if (isn) {
+                        const int p = jj;
+                        if (p < half) {
+                            if (q <= p) { r = p; cc = q; }
+                            else { r = NE - 1 - p; cc = q - p - 1; }
+                        } else if (q >= NE - half) {   // diagonals of the rows paired above
+                            r = q; cc = q;
+                        } else if ((NE & 1) && q <= half) {   // odd NE: the middle row
+                            r = half; cc = q;
+                        } else {
+                            r = -1; cc = 0;
+                        }
+                    } else {
+                        r = (s & 1) + 2 * (jj - n_nes);
+                        cc = q;
+                    }
+                    long long o = (isn ? off_n : off_p) + (long long)(r < 0 ? 0 : r) * NE + cc;
+                    // NMC_DEBUG: a corner outside the table is not read (entry skipped, offset 0 read instead)
+                    const bool tab_ok = isn ? NMC_IN_BOUNDS(g.dbg, o + sT + sE, tb.n_nes, kDbgNesTable)
+                                            : NMC_IN_BOUNDS(g.dbg, o + sT + sE, tb.n_pair, kDbgPairTable);
+                    if (!tab_ok) o = 0;
+                    rr[u] = (j0 + u < njobs && tab_ok) ? r : -1;
+                    cl[u] = cc;
+                    if constexpr (kMixed) {
+                        const float* tf = isn ? tnf : tpf;
+                        t[u][0] = __ldg(tf + o); t[u][1] = __ldg(tf + o + sT);
+                        t[u][2] = __ldg(tf + o + sE); t[u][3] = __ldg(tf + o + sT + sE);
+                    } else {
+                        const double* td = isn ? tn : tp;
+                        t[u][0] = __ldg(td + o); t[u][1] = __ldg(td + o + sT);
+                        t[u][2] = __ldg(td + o + sE); t[u][3] = __ldg(td + o + sT + sE);
+                    }
                 }
-            }
-            if (pair_on && s < NS) {
-                const int pr = s >> 1;
-                const R c = kMixed ? (R)os->pre_f[3] : (R)os->pre[3];
-                const long long off = (((long long)pr * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
-                R* A0 = AN + pr * NE * LD;
-                for (int idx = (s & 1) * GS + q; idx < NE * NE; idx += 2 * GS) {
-                    const int r = idx / NE, cc = idx - r * NE;
-                    const long long o = off + idx;
-                    if (!NMC_IN_BOUNDS(g.dbg, o + sT + sE, tb.n_pair, kDbgPairTable) ||
-                        !NMC_IN_BOUNDS(g.dbg, (long long)pr * NE * LD + r * LD + cc, (long long)(NS / 2) * NE * LD,
-                                       kDbgSmemPair))
-                        continue;
-                    R v;
-                    if (kMixed) v = w00 * tpf[o] + w10 * tpf[o + sT] + w01 * tpf[o + sE] + w11 * tpf[o + sT + sE];
-                    else v = w00 * tp[o] + w10 * tp[o + sT] + w01 * tp[o + sE] + w11 * tp[o + sT + sE];
-                    A0[r * LD + cc] = c * v;
+#pragma unroll
+                for (int u = 0; u < kB; ++u) {
+                    const int r = rr[u], cc = cl[u];
+                    if (r < 0) continue;
+                    const bool isn = j0 + u < n_nes;
+                    const R v = w00 * t[u][0] + w10 * t[u][1] + w01 * t[u][2] + w11 * t[u][3];
+                    if (isn) {
+                        if (!NMC_IN_BOUNDS(g.dbg, (long long)s * NE * LD + r * LD + cc, (long long)NS * NE * LD, kDbgSmemNes) ||
+                            !NMC_IN_BOUNDS(g.dbg, (long long)s * NE * LD + cc * LD + r, (long long)NS * NE * LD, kDbgSmemNes))
+                            continue;
+                        const R k = c_n * v;
+                        P0[r * LD + cc] = k;
+                        if (cc < r) P0[cc * LD + r] = va[r] * vai[cc] * k;
+                    } else {
+                        if (!NMC_IN_BOUNDS(g.dbg, (long long)pr * NE * LD + r * LD + cc, (long long)(NS / 2) * NE * LD,
+                                           kDbgSmemPair))
+                            continue;
+                        A0[r * LD + cc] = c_p * v;
+                    }
                 }
             }
         };
         fill(tb.nes, tb.nes_f, tb.pair, tb.pair_f, b.phi, b.ann);
         // linear-order kernels: the same interpolation, scale factors and relations (in-out invariance,
         // detailed balance) as the isotropic ones
-        const bool lin = !kMixed && b.phi1 != nullptr && tb.nes1 != nullptr;
-        if (lin) fill(tb.nes1, nullptr, tb.pair1, nullptr, b.phi1, b.ann1);
-        __syncthreads();
-        // up-scattering by detailed balance: K[r][c] = a_c / a_r K[c][r], r < c
-        auto upper = [&](R* PH) {
-            if (nes_on && s < NS) {
-                R* P0 = PH + s * NE * LD;
-                const R* va = b.vA + s * NEP;
-                const R* vai = b.vAi + s * NEP;
-                const int nup = NE * (NE - 1) / 2;   // strictly upper entries, column by column
-                for (int idx = q; idx < nup; idx += GS) {
-                    int cc = (int)((sqrtf(8.0f * idx + 1.0f) + 1.0f) * 0.5f);
-                    while (cc * (cc - 1) / 2 > idx) --cc;
-                    while ((cc + 1) * cc / 2 <= idx) ++cc;
-                    const int r = idx - cc * (cc - 1) / 2;
-                    if (!NMC_IN_BOUNDS(g.dbg, (long long)s * NE * LD + cc * LD + r, (long long)NS * NE * LD, kDbgSmemNes) ||
-                        !NMC_IN_BOUNDS(g.dbg, (long long)s * NE * LD + r * LD + cc, (long long)NS * NE * LD, kDbgSmemNes) ||
-                        !NMC_IN_BOUNDS(g.dbg, cc, NEP, kDbgSmemVec))
-                        continue;
-                    P0[r * LD + cc] = va[cc] * vai[r] * P0[cc * LD + r];
-                }
-            }
-        };
-        upper(b.phi);
-        if (lin) upper(b.phi1);
+        if (!kMixed && b.phi1 != nullptr && tb.nes1 != nullptr) fill(tb.nes1, nullptr, tb.pair1, nullptr, b.phi1, b.ann1);
     }
     __syncthreads();
-}
-
-// ComputeOpacities with one bin per thread: thread (s, q) = s * nep + q.
-template <typename R>
-__device__ __forceinline__ void compute_opacities(const DevGrid& g, const DevTables& tb, const nmc_params& P,
-                                                  double rho, double T, double Ye, double dtau, const double* sc,
-                                                  const OpacBufs<R>& b, OpacState* os, int* status, R& chiab, R& sig,
-                                                  R& deq, R& deqc, int lead = 0) {
-    R c[1] = {chiab}, si[1] = {sig}, d[1] = {deq}, dc[1] = {deqc};
-    compute_opacities_b<R, 1>(g, tb, P, rho, T, Ye, dtau, sc, b, os, status, c, si, d, dc, lead);
-    chiab = c[0];
-    sig = si[0];
-    deq = d[0];
-    deqc = dc[0];
 }
 
 }  // namespace nmc

@@ -100,14 +100,17 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
 
     R* phi = reinterpret_cast<R*>(smb + a.off_phi);   // [NS][NE][LD]   K_Out per species
     R* ann = reinterpret_cast<R*>(smb + a.off_ann);   // [NS/2][NE][LD] K_Ann per pair (particle)
-    // FP64: the contraction vectors in four arrays.  Mixed: one float4 per bin holding the same four
-    // (W~ D, W~ (1 - D), a W~ (1 - D), w), so that one 16-byte broadcast load gives a bin's every
-    // operand of the NES (own species) or pair (partner species) sums.
+    // FP64: the contraction vectors in four arrays.  Mixed: two float2 arrays, xw[s][j] = (W~ D, w)
+    // and yz[s][j] = (W~ (1 - D) of species s, a W~ (1 - D) of its partner s ^ 1), so that three
+    // 8-byte broadcast loads give a bin j's every operand of the NES (own species) and pair (partner
+    // species) sums.  An 8-byte broadcast costs the shared-memory pipe about as much as a 4-byte one,
+    // a 16-byte broadcast more than twice as much.
     R* vWD = reinterpret_cast<R*>(smb + a.off_vec);   // [NS][NEP] W~ D
     R* vW1D = vWD + NS * NEP;                          //           W~ (1 - D)
     R* vAW1D = vW1D + NS * NEP;                        //           a W~ (1 - D)
     R* vWdev = vAW1D + NS * NEP;                       //           w = W~ (D - D^Eq) / (1 - D^Eq) (mixed)
-    float4* v4 = reinterpret_cast<float4*>(smb + a.off_vec);   // mixed: [NS][NEP] (W~D, W~(1-D), aW~(1-D), w)
+    float2* xw = reinterpret_cast<float2*>(smb + a.off_vec);   // mixed: [NS][NEP] (W~D, w)
+    float2* yz = xw + NS * NEP;                                  //        [NS][NEP] (W~(1-D), partner's aW~(1-D))
     R* vA = vWdev + NS * NEP;                          //           a = D^Eq / (1 - D^Eq)
     R* vAi = vA + NS * NEP;                            //           1 / a
     R* vDeq = vAi + NS * NEP;                          //           D^Eq
@@ -268,7 +271,9 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         myW1D = Wt * hole;
                         myAW1D = aq * Wt * hole;
                         myWdev = __fadd_rn(__fsub_rn(D2.h, (float)deq), D2.l) * (Wt / deqc);
-                        v4[sq] = make_float4(Wt * D32, myW1D, myAW1D, myWdev);
+                        xw[sq] = make_float2(Wt * D32, myWdev);
+                        yz[sq].x = myW1D;
+                        yz[(s ^ 1) * NEP + q].y = myAW1D;
                     } else {
                         vWD[sq] = Wt * D32;
                         vW1D[sq] = Wt * hole;
@@ -299,31 +304,31 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                     R nin = 0, nout = 0, pro = 0, an = 0;
                     R cn = 0, cp = 0;   // mixed: net NES / pair exchange terms (deviation form)
                     if (kMixed && nes_on && pair_on) {
-                        // both sums in one pass over j (the terms as in the separate loops below),
-                        // each bin's operands from one 16-byte broadcast load per species
+                        // both sums in one pass over j (the terms as in the separate loops below)
                         const R* P0 = phi + s * NE * LD;
                         const int pt = s ^ 1;
                         const R* A0 = ann + (s >> 1) * NE * LD;
                         const bool part = (s & 1) == 0;
                         const int stride_j = part ? 1 : LD;
                         const int base = part ? q * LD : q;
-                        const float4* Vo = v4 + s * NEP;
-                        const float4* Vp = v4 + pt * NEP;
+                        const float2* Xo = xw + s * NEP;
+                        const float2* Xp = xw + pt * NEP;
+                        const float2* Yo = yz + s * NEP;
                         const R wq = myWdev, vq = myW1D;
                         R cw = 0;
 #pragma unroll 2
                         for (int j = 0; j < NE; ++j) {
-                            const float4 u = Vo[j], t = Vp[j];
+                            const float2 u = Xo[j], t = Xp[j], y = Yo[j];   // y.x: own W~(1-D), y.y: partner's aW~(1-D)
                             const R kin = P0[j * LD + q], kout = P0[q * LD + j];
                             nin = r_fma(kin, u.x, nin);
-                            nout = r_fma(kout, u.y, nout);
-                            const R e1 = __fmul_rn(kin, __fmul_rn(u.w, vq));
-                            const R e2 = __fmul_rn(kout, __fmul_rn(wq, u.y));
+                            nout = r_fma(kout, y.x, nout);
+                            const R e1 = __fmul_rn(kin, __fmul_rn(u.y, vq));
+                            const R e2 = __fmul_rn(kout, __fmul_rn(wq, y.x));
                             cn = __fadd_rn(cn, __fsub_rn(e1, e2));
                             const R av = A0[base + j * stride_j];
-                            pro = r_fma(av, t.z, pro);
+                            pro = r_fma(av, y.y, pro);
                             an = r_fma(av, t.x, an);
-                            cw = r_fma(av, t.w, cw);
+                            cw = r_fma(av, t.y, cw);
                         }
                         cp = -r_fma(myWdev, cw + pro, myAW1D * cw);
                         pro *= aq;
@@ -345,15 +350,17 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                             // map conserves number to the rounding of the sums: NES then leaves no
                             // rounding source in the slowly damped number-conserving mode (factored
                             // into dot products, it raised the heavy flavours' error 20-fold).
-                            const float4* Vo = v4 + s * NEP;
+                            const float2* Xo = xw + s * NEP;
+                            const float2* Yo = yz + s * NEP;
                             const R wq = myWdev, vq = myW1D;
                             for (int j = 0; j < NE; ++j) {
-                                const float4 u = Vo[j];
+                                const float2 u = Xo[j];
+                                const R yj = Yo[j].x;
                                 const R kin = P0[j * LD + q], kout = P0[q * LD + j];
                                 nin = r_fma(kin, u.x, nin);        // K_In[q][j] = K_Out[j][q]
-                                nout = r_fma(kout, u.y, nout);
-                                const R e1 = __fmul_rn(kin, __fmul_rn(u.w, vq));
-                                const R e2 = __fmul_rn(kout, __fmul_rn(wq, u.y));
+                                nout = r_fma(kout, yj, nout);
+                                const R e1 = __fmul_rn(kin, __fmul_rn(u.y, vq));
+                                const R e2 = __fmul_rn(kout, __fmul_rn(wq, yj));
                                 cn = __fadd_rn(cn, __fsub_rn(e1, e2));
                             }
                         } else {
@@ -379,13 +386,14 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         const int base = part ? q * LD : q;
                         R cw = 0;
                         if constexpr (kMixed) {
-                            const float4* Vp = v4 + pt * NEP;
+                            const float2* Xp = xw + pt * NEP;
+                            const float2* Yo = yz + s * NEP;
                             for (int j = 0; j < NE; ++j) {
-                                const float4 t = Vp[j];
+                                const float2 t = Xp[j];
                                 const R av = A0[base + j * stride_j];
-                                pro = r_fma(av, t.z, pro);
+                                pro = r_fma(av, Yo[j].y, pro);
                                 an = r_fma(av, t.x, an);
-                                cw = r_fma(av, t.w, cw);
+                                cw = r_fma(av, t.y, cw);
                             }
                             cp = -r_fma(myWdev, cw + pro, myAW1D * cw);
                         } else {
