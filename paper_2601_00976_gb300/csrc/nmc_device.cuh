@@ -9,6 +9,8 @@
 // 32, so a species group never straddles a warp unevenly.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -804,10 +806,87 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                 }
             }
         };
-        fill(tb.nes, tb.nes_f, tb.pair, tb.pair_f, b.phi, b.ann);
+        // The same fill with 16-byte table loads (kV entries of a row per load), when rows split into
+        // whole 16-byte chunks (NE a multiple of kV; the tables' rows then start on 16-byte boundaries).
+        //  NES: row pair (p, NE-1-p) covers its lower-triangle columns in NE/kV + 1 chunks (the last chunk
+        //  of a row may reach above the diagonal; those entries are not stored).  Pair: the group's rows
+        //  in NE/kV chunks each.  Chunks are dealt to the lanes of the species group in turn.
+        constexpr int kV = 16 / (int)sizeof(R);
+        using VecR = typename std::conditional<kMixed, float4, double2>::type;
+        auto fill_vec = [&](const double* tn, const float* tnf, const double* tp, const float* tpf, R* PH, R* AN) {
+            if (s >= NS) return;
+            const int nc = NE / kV, pr = s >> 1;
+            auto corners = [&](const double* td, const float* tf, long long o, R (&v)[kV]) {
+                const VecR* p00 = reinterpret_cast<const VecR*>(kMixed ? (const void*)(tf + o) : (const void*)(td + o));
+                const long long vT = sT / kV, vE = sE / kV;
+                const VecR a = __ldg(p00), bq = __ldg(p00 + vT), cq = __ldg(p00 + vE), dq = __ldg(p00 + vT + vE);
+                const R* ra = reinterpret_cast<const R*>(&a);
+                const R* rb = reinterpret_cast<const R*>(&bq);
+                const R* rc = reinterpret_cast<const R*>(&cq);
+                const R* rd = reinterpret_cast<const R*>(&dq);
+#pragma unroll
+                for (int i = 0; i < kV; ++i) v[i] = w00 * ra[i] + w10 * rb[i] + w01 * rc[i] + w11 * rd[i];
+            };
+            if (nes_on) {
+                const R c_n = kMixed ? (R)os->pre_f[2] : (R)os->pre[2];
+                const long long off_n = (((long long)s * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
+                R* P0 = PH + s * NE * LD;
+                const R* va = b.vA + s * NEP;
+                const R* vai = b.vAi + s * NEP;
+                const int per = nc + 1, total = (NE >> 1) * per;
+#pragma unroll 2
+                for (int c = q; c < total; c += GS) {
+                    const int p = c / per, k = c - p * per, kp = p / kV + 1;
+                    const int r = k < kp ? p : NE - 1 - p;
+                    const int c0 = (k < kp ? k : k - kp) * kV;
+                    const long long o = off_n + (long long)r * NE + c0;
+                    if (!NMC_IN_BOUNDS(g.dbg, o + sT + sE + kV - 1, tb.n_nes, kDbgNesTable) ||
+                        !NMC_IN_BOUNDS(g.dbg, (long long)s * NE * LD + r * LD + c0 + kV - 1, (long long)NS * NE * LD, kDbgSmemNes) ||
+                        !NMC_IN_BOUNDS(g.dbg, (long long)s * NE * LD + (c0 + kV - 1) * LD + r, (long long)NS * NE * LD, kDbgSmemNes))
+                        continue;
+                    R v[kV];
+                    corners(tn, tnf, o, v);
+                    const R ar = va[r];
+#pragma unroll
+                    for (int i = 0; i < kV; ++i) {
+                        const int col = c0 + i;
+                        if (col > r) break;
+                        const R kk = c_n * v[i];
+                        P0[r * LD + col] = kk;
+                        if (col < r) P0[col * LD + r] = ar * vai[col] * kk;
+                    }
+                }
+            }
+            if (pair_on) {
+                const R c_p = kMixed ? (R)os->pre_f[3] : (R)os->pre[3];
+                const long long off_p = (((long long)pr * tb.kt.n + os->ikt) * tb.eta.n + os->ike) * mat;
+                R* A0 = AN + pr * NE * LD;
+                const int total = ((NE - (s & 1) + 1) >> 1) * nc;
+#pragma unroll 2
+                for (int c = q; c < total; c += GS) {
+                    const int rr2 = c / nc, c0 = (c - rr2 * nc) * kV;
+                    const int r = (s & 1) + 2 * rr2;
+                    const long long o = off_p + (long long)r * NE + c0;
+                    if (!NMC_IN_BOUNDS(g.dbg, o + sT + sE + kV - 1, tb.n_pair, kDbgPairTable) ||
+                        !NMC_IN_BOUNDS(g.dbg, (long long)pr * NE * LD + r * LD + c0 + kV - 1, (long long)(NS / 2) * NE * LD,
+                                       kDbgSmemPair))
+                        continue;
+                    R v[kV];
+                    corners(tp, tpf, o, v);
+#pragma unroll
+                    for (int i = 0; i < kV; ++i) A0[r * LD + c0 + i] = c_p * v[i];
+                }
+            }
+        };
+        const bool vec = NE % kV == 0;
+        if (vec) fill_vec(tb.nes, tb.nes_f, tb.pair, tb.pair_f, b.phi, b.ann);
+        else fill(tb.nes, tb.nes_f, tb.pair, tb.pair_f, b.phi, b.ann);
         // linear-order kernels: the same interpolation, scale factors and relations (in-out invariance,
         // detailed balance) as the isotropic ones
-        if (!kMixed && b.phi1 != nullptr && tb.nes1 != nullptr) fill(tb.nes1, nullptr, tb.pair1, nullptr, b.phi1, b.ann1);
+        if (!kMixed && b.phi1 != nullptr && tb.nes1 != nullptr) {
+            if (vec) fill_vec(tb.nes1, nullptr, tb.pair1, nullptr, b.phi1, b.ann1);
+            else fill(tb.nes1, nullptr, tb.pair1, nullptr, b.phi1, b.ann1);
+        }
     }
     __syncthreads();
 }

@@ -183,6 +183,26 @@ def test_ne64_grid_f_sampled():
     ctx.close()
 
 
+@pytest.mark.parametrize("n_elem", [15, 18])
+def test_rows_not_multiple_of_vector_width(n_elem):
+    """Constant elements with NE = 15 (odd) and NE = 18 (even, not a multiple of 4): the kernel tables are
+    filled entry by entry where NE is not a multiple of the 16-byte load width (4 FP32 or 2 FP64
+    entries), and in 2-entry loads for FP64 at NE = 18.  FP64 at the parity bar and the mixed path at
+    1e-5, both against the oracle, full physics."""
+    edges, g, tables, inp = make_case(n_elem, 3.0, 1, 4, "profile", 6, seed=82)
+    ctx = _ctx(edges, 1, 4, tables)
+    ref = _oracle(g, tables, inp, range(6), **TIGHT)
+    out = gpu_solve(ctx, inp, **TIGHT)
+    for n, r in enumerate(ref):
+        compare_node(out, n, r, g.W2, PARITY)
+    mix = gpu_solve(ctx, inp, precision=nmc.MIXED, tol_inner=1e-11, tol_outer=1e-10, max_inner=2000, max_outer=100)
+    for n, r in enumerate(ref):
+        eD, eI = wnorm_errors(mix["J"][n], mix["H"][n], r["D"], r["I"], g.W2)
+        assert eD.max() <= 1e-5 and eI.max() <= 1e-5, (n, eD, eI)
+        assert mix["status"][n] == 0
+    ctx.close()
+
+
 def test_six_species_symmetry_and_parity():
     edges, g, tables, inp = make_case(4, 20.0, 2, 6, "profile", 16, seed=13, table_seed=5)
     for key in ("emab", "iso", "nes"):
