@@ -74,8 +74,8 @@ WORKLOAD = ("perturbed collapse profile (+-10% seeded perturbations of rho, T, Y
 # DRAM bytes (read + write) per node of one launch, from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum); traffic grows with the node count.  None where the kernel has changed since its
 # counters were taken.
-TRAFFIC_PER_NODE = {"fused_kernel<double>": None, "fused_kernel<float>": None,
-                    "adjoint_kernel": 203109376 / 16384, "velocity_kernel": 524328704 / 65536,
+TRAFFIC_PER_NODE = {"fused_kernel<double>": 255172096 / 16384, "fused_kernel<float>": 240471040 / 16384,
+                    "adjoint_kernel": 203126272 / 16384, "velocity_kernel": 101233152 / 16384,
                     "c2p_kernel": 530723584 / 65536, "opacity_interp_kernel": 159e6 / (1 << 22),
                     "opacity_interp_mixed_kernel": 162e6 / (1 << 22)}
 
@@ -334,7 +334,7 @@ def _measured_hbm_gbs():
 
 HBM_PEAK_GBS = _measured_hbm_gbs()
 # FMA-pipe peaks (TFLOP/s), measured by measure_peaks() at the start of a run
-PEAKS = {"fp64": None, "fp32": None}
+PEAKS = {"fp64": None, "fp32": None, "smem_gbs": None, "smem_relative_cost": None}
 PEAK_NOTE = "measured: nmc_fma_probe (16 independent FMA chains per thread, full occupancy, CUDA events)"
 
 
@@ -358,6 +358,28 @@ def measure_peaks(stream, reps=5, warm=10):
             e1.synchronize()
             best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e12)
         out[name] = best
+    # shared-memory pipe: lane-consecutive 4-byte loads (128 bytes per warp load), GB/s, and the cost of
+    # the other load kinds per warp load relative to it
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    per_load = {}
+    for mode in range(5):
+        for _ in range(3):
+            nmc.smem_probe(mode, 200, sink, stream=stream)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            loads = nmc.smem_probe(mode, 200, sink, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3 / loads)
+        per_load[mode] = best
+    out["smem_gbs"] = 128.0 / per_load[nmc.SMEM_B32_CONSECUTIVE] / 1e9
+    base = per_load[nmc.SMEM_B32_CONSECUTIVE]
+    out["smem_relative_cost"] = {"b32_broadcast": per_load[nmc.SMEM_B32_BROADCAST] / base,
+                                 "b64_broadcast": per_load[nmc.SMEM_B64_BROADCAST] / base,
+                                 "b128_broadcast": per_load[nmc.SMEM_B128_BROADCAST] / base,
+                                 "b128_consecutive": per_load[nmc.SMEM_B128_CONSECUTIVE] / base}
     return out
 
 
@@ -886,6 +908,19 @@ def run_nmc(args):
                                   "/ FP64 peak over the launch's algorithmic work"),
                   "algorithmic_flops_per_launch": rmx["flops"], "algorithmic_fp64_flops_per_launch": f64w,
                   "bound_ms": t_bound * 1e3, "kernel_ms": rmx["kern_ms"]}
+        # the contraction loop's own bound: every inner iteration reads each node's kernel matrices from
+        # shared memory, K_Out of each species twice (rows and columns) and K_Ann of each pair by both of
+        # its species, 12 ns ne^2 bytes in FP32, against the shared-memory pipe's rate measured by
+        # nmc_smem_probe (lane-consecutive 4-byte loads, one 128-byte wavefront per warp load)
+        clk_sum = clk.summary()
+        smem_bytes = float(rmx["n_in"].sum()) * 12.0 * NS * ne * ne
+        smem_ach = smem_bytes / (rmx["kern_ms"] * 1e-3) / 1e9
+        roof_smem = {"bound": "smem", "achieved": smem_ach, "peak": PEAKS["smem_gbs"], "unit": "GB/s",
+                     "frac": smem_ach / PEAKS["smem_gbs"], "kernel": "fused_kernel<float>",
+                     "algorithmic_bytes_per_launch": smem_bytes,
+                     "model": "kernel-matrix operands of the inner iterations (12 ns ne^2 bytes per node-iteration)",
+                     "peak_source": "measured: nmc_smem_probe, lane-consecutive 4-byte loads (CUDA events)",
+                     "probe_cost_per_warp_load_relative_to_one_wavefront": PEAKS["smem_relative_cost"]}
         value = line_value(rmx, args.steps)
         cfg = {"workload": WORKLOAD, "precision": "mixed", "nodes_per_gpu": args.nodes,
                "l2": "inputs_larger_than_l2", "tolerances": {"fp64": [TOL, TOL], "mixed": list(MIXED_TOL)},
@@ -912,10 +947,12 @@ def run_nmc(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": cfg,
             "roofline": roofmx,
+            "roofline_smem": roof_smem,
             "roofline_fp64": roof64(r64) if r64 is not None else None,
-            "peaks_measured": {"fp64_tflops": PEAKS["fp64"], "fp32_tflops": PEAKS["fp32"], "how": PEAK_NOTE},
+            "peaks_measured": {"fp64_tflops": PEAKS["fp64"], "fp32_tflops": PEAKS["fp32"], "how": PEAK_NOTE,
+                               "smem_gbs": PEAKS["smem_gbs"]},
             "gpu_launches": args.steps,
-            "clocks": clk.summary(),
+            "clocks": clk_sum,
         }
         if e2e is not None:
             line["e2e"] = e2e

@@ -196,6 +196,24 @@ const char* nmc_last_error(const nmc_ctx* ctx);
  */
 int nmc_debug_word(nmc_ctx* ctx, uint32_t* word, int32_t clear);
 
+/*
+ * Stage counters of the NMC_TRACE build (a profiling aid; the paper has no
+ * counterpart).  The library built with -DNMC_TRACE has thread 0 of every block
+ * of the fused collision-solve kernel read the SM cycle counter at each stage
+ * boundary of Algorithm 1 and add, when the block ends, the cycles spent in
+ * each stage to a counter of the context: 0 node set-up, 1 ComputeOpacities,
+ * 2 reference norms and first vectors of an outer iteration, 3 contraction
+ * loop and map Q, 4 least-squares partial sums, 5 least-squares solve,
+ * 6 Anderson mixing and next vectors, 7 Algorithm 2 vote, 8 matter update,
+ * 9 final state and outputs, 10 taking the next node (counters 11-15 are
+ * zero).  The counts are block time (barrier waits and cycles the SM gives to
+ * other blocks included), summed over blocks.  This call copies the 16
+ * counters to the HOST array `cycles`, clearing them when `clear` is nonzero;
+ * it waits for the device.  The release build returns NMC_EUNSUPPORTED with
+ * the counters zeroed.
+ */
+int nmc_trace_read(nmc_ctx* ctx, uint64_t* cycles, int32_t clear);
+
 /* Writes the node energies eps_q (MeV), W2_q (cm^-3) and W3_q (MeV cm^-3) of
  * the context's grid into HOST arrays of length ne (any may be NULL). */
 int nmc_energy_nodes(const nmc_ctx* ctx, double* eps, double* w2, double* w3, int32_t* ne);
@@ -470,6 +488,27 @@ int collision_adjoint(nmc_ctx* ctx, const nmc_params* params, int64_t n,
  */
 int nmc_fma_probe(int32_t precision, int32_t blocks_per_sm, int32_t iters, void* sink, double* flops,
                   void* stream);
+
+/*
+ * Shared-memory load probe (a measurement helper; the paper has no
+ * counterpart).  The mixed kernel's contraction loop reads each node's kernel
+ * matrices from shared memory every inner iteration, so the shared-memory pipe
+ * bounds it.  Launches, on `stream`, one kernel of 1024-thread blocks (as many
+ * per SM as fit, 16 KB of static shared memory each) in which every warp issues
+ * iters x 64 loads of one kind:
+ *   mode 0  4-byte loads of 32 consecutive words (one 128-byte wavefront: the
+ *           pipe's peak rate);
+ *   mode 1  4-byte warp-uniform (broadcast) loads;
+ *   mode 2  8-byte broadcast loads;
+ *   mode 3  16-byte broadcast loads;
+ *   mode 4  16-byte loads of consecutive words (512 bytes per warp load).
+ * Stores in *warp_loads the launch's warp-load count; the caller times the
+ * launch with CUDA events on `stream` (mode 0: 128 bytes per warp load).
+ * sink: DEVICE buffer of one float, written only to keep the loads live.
+ * NMC_EINVAL for iters < 1, a NULL sink or another mode; NMC_ECUDA for a
+ * failed launch.
+ */
+int nmc_smem_probe(int32_t mode, int32_t iters, void* sink, double* warp_loads, void* stream);
 
 #ifdef __cplusplus
 }

@@ -18,6 +18,9 @@ LIB = os.path.join(OUT, "libnmc.so")
 # the NMC_DEBUG build (bounds checks that record a failed index in a device error word)
 OUT_DEBUG = os.path.join(HERE, "_lib_debug")
 LIB_DEBUG = os.path.join(OUT_DEBUG, "libnmc.so")
+# the NMC_TRACE build (per-stage SM-cycle counters of the fused kernel)
+OUT_TRACE = os.path.join(HERE, "_lib_trace")
+LIB_TRACE = os.path.join(OUT_TRACE, "libnmc.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -41,10 +44,13 @@ def _headers_mtime():
     return max((os.path.getmtime(p) for p in paths), default=0.0)
 
 
-def build(verbose=False, force=False, debug=False):
-    """Compile and link libnmc.so (debug: the NMC_DEBUG build, in its own folder); returns its path."""
-    out, lib = (OUT_DEBUG, LIB_DEBUG) if debug else (OUT, LIB)
-    flags = FLAGS + (["-DNMC_DEBUG"] if debug else [])
+def build(verbose=False, force=False, debug=False, trace=False):
+    """Compile and link libnmc.so (debug: the NMC_DEBUG build; trace: the NMC_TRACE build; each in its
+    own folder); returns its path."""
+    if debug and trace:
+        raise ValueError("the NMC_DEBUG and NMC_TRACE builds are separate")
+    out, lib = (OUT_DEBUG, LIB_DEBUG) if debug else ((OUT_TRACE, LIB_TRACE) if trace else (OUT, LIB))
+    flags = FLAGS + (["-DNMC_DEBUG"] if debug else []) + (["-DNMC_TRACE"] if trace else [])
     os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
     hdr = _headers_mtime()
@@ -71,4 +77,4 @@ def build(verbose=False, force=False, debug=False):
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv, debug="--debug" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, debug="--debug" in sys.argv, trace="--trace" in sys.argv))

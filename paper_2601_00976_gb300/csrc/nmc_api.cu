@@ -164,6 +164,20 @@ const char* nmc_last_error(const nmc_ctx* ctx) {
     return ctx->last_error.c_str();
 }
 
+int nmc_trace_read(nmc_ctx* ctx, uint64_t* cycles, int32_t clear) {
+    if (!ctx || !cycles) return NMC_EINVAL;
+    for (int i = 0; i < kTraceWords; ++i) cycles[i] = 0;
+#ifdef NMC_TRACE
+    cudaError_t e = cudaMemcpy(cycles, ctx->g.trace, kTraceWords * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && clear) e = cudaMemset(ctx->g.trace, 0, kTraceWords * sizeof(uint64_t));
+    if (e != cudaSuccess) return set_error(ctx, NMC_ECUDA, std::string("nmc_trace_read: ") + cudaGetErrorString(e));
+    return NMC_OK;
+#else
+    (void)clear;
+    return NMC_EUNSUPPORTED;
+#endif
+}
+
 int nmc_debug_word(nmc_ctx* ctx, uint32_t* word, int32_t clear) {
     if (!ctx || !word) return NMC_EINVAL;
     *word = 0;
@@ -383,6 +397,15 @@ int nmc_create(const nmc_grid* grid, const nmc_tables* tb, nmc_ctx** out) {
         if (e == cudaSuccess) e = cudaMemset(p, 0, 256);
         if (e != cudaSuccess) rc = NMC_ENOMEM;
         else { ctx->allocations.push_back(p); ctx->g.dbg = static_cast<unsigned*>(p); }
+    }
+#endif
+#ifdef NMC_TRACE
+    if (rc == NMC_OK) {   // the stage counters, cleared
+        void* p = nullptr;
+        e = cudaMalloc(&p, kTraceWords * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemset(p, 0, kTraceWords * sizeof(unsigned long long));
+        if (e != cudaSuccess) rc = NMC_ENOMEM;
+        else { ctx->allocations.push_back(p); ctx->g.trace = static_cast<unsigned long long*>(p); }
     }
 #endif
     // Set-up of collision_solve_noalloc, done here because this call may allocate: load the fused

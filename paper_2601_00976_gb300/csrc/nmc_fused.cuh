@@ -143,6 +143,14 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         for (int c = 0; c < 4; ++c) Qh[j][c] = 0;
     }
 
+#ifdef NMC_TRACE
+    unsigned long long tr[kTrStages] = {};
+    long long tr_t = clock64();
+    // thread 0 adds the cycles since the previous boundary to stage st
+#define NMC_TRACE_TICK(st) do { if (tid == 0) { const long long t1_ = clock64(); tr[st] += t1_ - tr_t; tr_t = t1_; } } while (0)
+#else
+#define NMC_TRACE_TICK(st) do { } while (0)
+#endif
     for (;;) {
         if (tid == 0) {
             long long nn = atomicAdd(a.queue, 1);
@@ -153,6 +161,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         }
         __syncthreads();
         const long long n = nd->node;
+        NMC_TRACE_TICK(kTrQueue);
         if (n >= a.n) break;
         // The node's scalar work (EoS, least squares, matter update) runs in lane 0 of one
         // warp.  A warp's FP64 instruction holds its SMSP's FP64 pipe ~64 cycles however
@@ -226,6 +235,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
         F2 Dx = f2_from(Dsd), A0x = {0.f, 0.f}, c12x = {0.f, 0.f};
         R chiab = 0, sig = 0, deq = 0, deqc = 0;
         int outer_exit = 0;
+        NMC_TRACE_TICK(kTrSetup);
 
         for (int k = 1;; ++k) {
             // ================= ComputeOpacities(y^[k]) =================
@@ -234,6 +244,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
             if (k == 1 || !P.semi_implicit)
                 compute_opacities<R>(g, a.tb, P, nd->rho, nd->T, nd->y[1], nd->dtau, nd->sc, ob, &nd->op,
                                      &nd->status, chiab, sig, deq, deqc, lead);
+            NMC_TRACE_TICK(kTrOpac);
             if constexpr (kMixed) {
                 const double c1 = (double)Wt, c2 = c1 * (double)chiab;
                 A0x = f2_from(c1 * Dsd + c2 * (double)deq);
@@ -283,6 +294,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
             };
             publish(M[0], Dx);
             __syncthreads();
+            NMC_TRACE_TICK(kTrNorms);
             bool inner_stop = false;   // the inner loop hit its cap or a non-finite moment
             // ================= inner loop =================
             // Three barriers an iteration: the Gram row's warp partials, the least-squares
@@ -473,8 +485,10 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         for (int j = 0; j < 3; ++j)
                             v[j] = F[0] * Fh[j][0] + F[1] * Fh[j][1] + F[2] * Fh[j][2] + F[3] * Fh[j][3];
                     }
+                    NMC_TRACE_TICK(kTrContract);
                     warp_partials<K, R>(v, red);
                     __syncthreads();
+                    NMC_TRACE_TICK(kTrGram);
                     if ((tid >> 5) == (lead >> 5)) {
                         const int k = tid & 31;
                         const R* pr = reinterpret_cast<const R*>(red);
@@ -493,6 +507,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         }
                     }
                     __syncthreads();
+                    NMC_TRACE_TICK(kTrSolve);
                 } else {   // new row of the Gram matrix; the lead adds the warps' partials and solves
                            // the least squares in FP64
                     R v[MAXM];
@@ -500,8 +515,10 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                     for (int j = 0; j < MAXM; ++j) {
                         v[j] = F[0] * Fh[j][0] + F[1] * Fh[j][1] + F[2] * Fh[j][2] + F[3] * Fh[j][3];
                     }
+                    NMC_TRACE_TICK(kTrContract);
                     warp_partials<MAXM, R>(v, red);
                     __syncthreads();
+                    NMC_TRACE_TICK(kTrGram);
                     if (tid == lead) {
                         R out[MAXM];
                         sum_partials<MAXM, R>(red, out);
@@ -515,6 +532,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                         for (int j = 0; j < MAXM; ++j) nd->alpha_f[j] = (float)nd->alpha[j];
                     }
                     __syncthreads();
+                    NMC_TRACE_TICK(kTrSolve);
                 }
                 R Mn[4];
 #pragma unroll
@@ -540,6 +558,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                     Mn[0] = Dxn.h;
                 }
                 publish(Mn[0], Dxn);
+                NMC_TRACE_TICK(kTrMix);
                 int vote = 1;
                 {   // Algorithm 2: per species, W-weighted squares of the change per moment
                     R v[4];
@@ -606,6 +625,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
 #pragma unroll
                     for (int j = 0; j < MAXM; ++j) Qh[j][0] -= sD;
                 }
+                NMC_TRACE_TICK(kTrVote);
                 if (conv || bad || ell >= P.max_inner) {
                     inner_stop = bad || capped;
                     break;
@@ -655,6 +675,7 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
                 __syncthreads();
                 if (nd->conv_out) outer_exit = 1;
             }
+            NMC_TRACE_TICK(kTrMatter);
             if (outer_exit) {
                 if (tid == lead) nd->n_outer = k;
                 break;
@@ -700,7 +721,13 @@ __global__ void __launch_bounds__(MAXT, MINB) fused_kernel(const SolveArgs a) {
             a.H_out[o * 3 + 2] = (double)M[3];
         }
         __syncthreads();
+        NMC_TRACE_TICK(kTrFinal);
     }
+#ifdef NMC_TRACE
+    if (tid == 0 && g.trace)
+        for (int st = 0; st < kTrStages; ++st) atomicAdd(g.trace + st, tr[st]);
+#endif
+#undef NMC_TRACE_TICK
 }
 
 template <typename R, int MAXM, int MAXT, int MINB>

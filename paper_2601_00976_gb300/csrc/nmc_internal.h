@@ -51,6 +51,27 @@ enum DebugSite : unsigned {
     kDbgProj = 10,        // projection operators
 };
 
+// Stage counters of the NMC_TRACE build: thread 0 of every block of the fused
+// kernel reads the SM cycle counter at each stage boundary and, when the block
+// ends, adds the cycles spent in each stage to trace[stage].  Block time, not
+// busy time: a stage's count includes its barrier waits and the cycles the
+// SM gives to other blocks meanwhile.  Release builds compile none of it.
+enum TraceStage {
+    kTrSetup = 0,     // node set-up: loads, EoS at the old state, E_nu*, N_nu*
+    kTrOpac = 1,      // ComputeOpacities
+    kTrNorms = 2,     // reference norms and the first vectors of an outer iteration
+    kTrContract = 3,  // contraction loop and map Q
+    kTrGram = 4,      // least-squares partial sums and their barrier
+    kTrSolve = 5,     // least-squares solve (lead warp) and its barrier
+    kTrMix = 6,       // Anderson mixing and the next vectors
+    kTrVote = 7,      // Algorithm 2 and the vote's barrier
+    kTrMatter = 8,    // matter update: sums, outer Anderson step, EoS root
+    kTrFinal = 9,     // final matter state and outputs
+    kTrQueue = 10,    // taking the next node from the queue
+    kTrStages = 11
+};
+constexpr int kTraceWords = 16;
+
 #ifdef NMC_DEBUG
 __device__ inline bool debug_in_bounds(unsigned* word, long long idx, long long n, unsigned site) {
     if (idx >= 0 && idx < n) return true;
@@ -89,6 +110,7 @@ struct DevGrid {
     double sum_w2;
     double sum_wt;
     unsigned* dbg;           // NMC_DEBUG builds: the context's bounds-check error word (null otherwise)
+    unsigned long long* trace;   // NMC_TRACE builds: per-stage SM-cycle counters (null otherwise)
 };
 
 struct DevTables {

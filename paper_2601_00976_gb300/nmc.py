@@ -16,9 +16,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# NMC_DEBUG=1 in the environment selects the bounds-checked build (built by
-# `python -m paper_2601_00976_gb300._build --debug`)
-LIB_PATH = os.path.join(_HERE, "_lib_debug" if os.environ.get("NMC_DEBUG") == "1" else "_lib", "libnmc.so")
+# NMC_DEBUG=1 in the environment selects the bounds-checked build, NMC_TRACE=1 the stage-counter build
+# (built by `python -m paper_2601_00976_gb300._build --debug` / `--trace`)
+LIB_PATH = os.path.join(_HERE, "_lib_debug" if os.environ.get("NMC_DEBUG") == "1" else
+                        ("_lib_trace" if os.environ.get("NMC_TRACE") == "1" else "_lib"), "libnmc.so")
 
 NMC_OK, NMC_EINVAL, NMC_ECUDA, NMC_ENOMEM, NMC_EUNSUPPORTED = 0, 1, 2, 3, 4
 NOT_CONVERGED_INNER, NOT_CONVERGED_OUTER, NONFINITE, EOS_FAIL, TABLE_CLAMP, BAD_INPUT = 1, 2, 4, 8, 16, 32
@@ -60,7 +61,8 @@ class Params(ctypes.Structure):
 
 EXPORTS = ("nmc_default_params", "nmc_create", "nmc_destroy", "nmc_last_error", "nmc_energy_nodes",
            "nmc_grid_nodes", "nmc_geometric_edges", "collision_solve", "collision_solve_noalloc", "collision_solve_v", "conserved_to_primitive",
-           "opacity_interp", "collision_adjoint", "nmc_set_plain_chunk", "nmc_autotune", "nmc_fma_probe", "collision_solve_host", "opacity_interp_mixed", "nmc_debug_word")
+           "opacity_interp", "collision_adjoint", "nmc_set_plain_chunk", "nmc_autotune", "nmc_fma_probe", "collision_solve_host", "opacity_interp_mixed", "nmc_debug_word",
+           "nmc_smem_probe", "nmc_trace_read")
 
 _lib = None
 
@@ -113,8 +115,12 @@ def load_library(path=LIB_PATH):
     lib.nmc_fma_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp,
                                   ctypes.POINTER(ctypes.c_double), vp]
     lib.nmc_fma_probe.restype = ctypes.c_int
+    lib.nmc_smem_probe.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, ctypes.POINTER(ctypes.c_double), vp]
+    lib.nmc_smem_probe.restype = ctypes.c_int
     lib.nmc_debug_word.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32]
     lib.nmc_debug_word.restype = ctypes.c_int
+    lib.nmc_trace_read.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32]
+    lib.nmc_trace_read.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -165,6 +171,23 @@ def fma_probe(precision, iters, sink, blocks_per_sm=0, stream=None):
     if rc != NMC_OK:
         raise NmcError(f"nmc_fma_probe failed with code {rc}")
     return flops.value
+
+
+# nmc_smem_probe modes
+SMEM_B32_CONSECUTIVE, SMEM_B32_BROADCAST, SMEM_B64_BROADCAST, SMEM_B128_BROADCAST, SMEM_B128_CONSECUTIVE = range(5)
+
+
+def smem_probe(mode, iters, sink, stream=None):
+    """Launch the shared-memory load probe on `stream` (torch's current one by default); returns the
+    launch's warp-load count.  sink: a one-element float32 CUDA tensor."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    loads = ctypes.c_double()
+    rc = load_library().nmc_smem_probe(int(mode), int(iters), ctypes.c_void_p(sink.data_ptr()), ctypes.byref(loads),
+                                       ctypes.c_void_p(s.cuda_stream))
+    if rc != NMC_OK:
+        raise NmcError(f"nmc_smem_probe failed with code {rc}")
+    return loads.value
 
 
 def _dptr(a):
@@ -224,6 +247,13 @@ class Context:
 
     def last_error(self):
         return self._lib.nmc_last_error(self._h).decode()
+
+    def trace_read(self, clear=False):
+        """The fused kernel's 16 stage counters (SM cycles of block time) of the NMC_TRACE build; raises
+        NmcError in other builds."""
+        c = (ctypes.c_uint64 * 16)()
+        self._check(self._lib.nmc_trace_read(self._h, c, 1 if clear else 0), "nmc_trace_read")
+        return [int(x) for x in c]
 
     def debug_word(self, clear=False):
         """The NMC_DEBUG build's bounds-check error word (0: no check failed); raises NmcError on a

@@ -3,7 +3,6 @@ exports the same entry points as the release build, and rejects inconsistent sha
 before any launch.  No GPU is needed; tests/test_gpu_debug.py runs its kernels."""
 
 import ctypes
-import os
 
 import numpy as np
 import pytest
@@ -14,8 +13,7 @@ from test_abi import declared_functions
 @pytest.fixture(scope="module")
 def dlib():
     from paper_2601_00976_gb300 import _build
-    if not os.path.exists(_build.LIB_DEBUG):
-        _build.build(debug=True)
+    _build.build(debug=True)   # incremental: recompiles the units whose sources changed
     return ctypes.CDLL(_build.LIB_DEBUG)
 
 

@@ -76,3 +76,26 @@ def test_fma_probe_rates_are_plausible():
     assert 20.0 <= rates["fp32"] <= 200.0, rates
     with pytest.raises(nmc.NmcError):
         nmc.fma_probe(nmc.FP64, 0, torch.zeros(1, dtype=torch.float64, device="cuda"))
+
+
+def test_smem_probe_rates_are_plausible():
+    """Lane-consecutive 4-byte loads move 128 bytes per warp load at about one warp load per SM cycle
+    (152 SMs at up to 2.07 GHz: ~40 TB/s); the broadcasts cost at least as much per load as one
+    wavefront, and a 16-byte load of consecutive words four wavefronts."""
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ms = {}
+    for mode in range(5):
+        nmc.smem_probe(mode, 50, sink)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        loads = nmc.smem_probe(mode, 200, sink)
+        e1.record()
+        e1.synchronize()
+        ms[mode] = e0.elapsed_time(e1) / loads
+    gbs = 128.0 / (ms[nmc.SMEM_B32_CONSECUTIVE] * 1e-3) / 1e9
+    assert 10e3 <= gbs <= 60e3, gbs
+    rel = {m: ms[m] / ms[nmc.SMEM_B32_CONSECUTIVE] for m in ms}
+    assert all(r >= 0.8 for r in rel.values()), rel
+    assert 3.0 <= rel[nmc.SMEM_B128_CONSECUTIVE] <= 5.0, rel
+    with pytest.raises(nmc.NmcError):
+        nmc.smem_probe(7, 10, sink)
