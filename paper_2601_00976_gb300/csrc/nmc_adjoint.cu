@@ -378,18 +378,45 @@ __global__ void __launch_bounds__(MAXT, MINB) adjoint_kernel(const AdjointArgs a
                         if (!NMC_IN_BOUNDS(g.dbg, P, N2, kDbgHistory)) break;
                         if (P < 64) done0 |= 1ull << P; else done1 |= 1ull << (P - 64);
                         if (tid == 0) nd->prow[c] = P;
-                        double nb = -1.0;
-                        int ni = 0;
-                        for (int r = warp; r < N2; r += nwarps) {
-                            if (is_done(r)) continue;
-                            const double l = Mt[r * LDM + c] * ip;
-                            for (int j = c + 1 + lane; j < N2 + 3; j += 32) Mt[r * LDM + j] -= l * Mt[P * LDM + j];
-                            if (lane == 0 && c + 1 < N2) {
-                                const double v = fabs(Mt[r * LDM + c + 1]);
-                                if (v > nb) { nb = v; ni = r; }
+                        // The warp's rows r = warp + nwarps i, 32 at a time: lane i forms row i's multiplier
+                        // (one FP64 instruction for 32 rows instead of one per row), the rows are updated one
+                        // after another with all lanes along j, and then lane i reads row i's new entry of
+                        // column c + 1.  The warp's candidate is the largest |entry|, the smallest row among
+                        // equals (as a scan in row order would pick): |entry| compared as the integer of its
+                        // bits (order-preserving for non-negative doubles; NaN is no candidate), so the
+                        // search issues no FP64 compare.
+                        const int rows_w = (N2 - warp + nwarps - 1) / nwarps;
+                        long long bkey = -1;   // best |entry| bits of this lane's rows (-1: none)
+                        int brow = 0;
+                        for (int i0 = 0; i0 < rows_w; i0 += 32) {
+                            const int rl = warp + nwarps * (i0 + lane);
+                            const bool ract = i0 + lane < rows_w && !is_done(rl);
+                            const double lmul = ract ? Mt[rl * LDM + c] * ip : 0.0;
+                            const int ng = rows_w - i0 < 32 ? rows_w - i0 : 32;
+                            for (int k = 0; k < ng; ++k) {
+                                const double l = __shfl_sync(kFull, lmul, k);
+                                const int r = warp + nwarps * (i0 + k);
+                                if (is_done(r)) continue;
+                                for (int j = c + 1 + lane; j < N2 + 3; j += 32) Mt[r * LDM + j] -= l * Mt[P * LDM + j];
+                            }
+                            __syncwarp();
+                            if (ract && c + 1 < N2) {
+                                const double v = fabs(Mt[rl * LDM + c + 1]);
+                                if (v == v) {
+                                    const long long key = __double_as_longlong(v);
+                                    if (key > bkey) { bkey = key; brow = rl; }
+                                }
                             }
                         }
+                        long long wkey = bkey;
+                        for (int off = 16; off > 0; off >>= 1) {
+                            const long long o = __shfl_xor_sync(kFull, wkey, off);
+                            wkey = o > wkey ? o : wkey;
+                        }
+                        const int wrow = (int)__reduce_min_sync(kFull, (unsigned)(bkey == wkey && wkey >= 0 ? brow : 0x7fffffff));
                         if (lane == 0) {
+                            const double nb = wkey >= 0 ? __longlong_as_double(wkey) : -1.0;
+                            const int ni = wkey >= 0 ? wrow : 0;
                             nd->cv[bsel ^ 1][warp] = nb;
                             nd->ci[bsel ^ 1][warp] = ni;
                             nd->cip[bsel ^ 1][warp] = nb > 0.0 ? 1.0 / Mt[ni * LDM + c + 1] : 0.0;
