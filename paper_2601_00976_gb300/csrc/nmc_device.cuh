@@ -538,17 +538,22 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
     // this function hit L2 at several hundred cycles each, so every stage issues its loads in
     // straight-line batches (indices clamped into range, the results' stores guarded): one
     // memory latency per batch instead of one per loop trip.
+    // The heavy flavours (species 2 and up) all have mu = 0, so they share species 2's values: the
+    // nfd <= 3 distinct species' points are dealt out over every thread of the block.
     {
         const int nqp = g.n_elem * kProjQuad;
+        const int nfd = NS < 3 ? NS : 3, nfdp = nfd * nqp;
         if (s < NS) {
-            const R mu = (R)os->mu[s], Tinv = (R)os->tinv;
-            const float muh = os->mu_h[s], mul = os->mu_l[s], tih = os->tinv_h, til = os->tinv_l;
-            for (int i0 = q; i0 < nqp; i0 += kFdBatch * GS) {
+            const R Tinv = (R)os->tinv;
+            const float tih = os->tinv_h, til = os->tinv_l;
+            const int nthr = NS * GS;
+            for (int k0 = s * GS + q; k0 < nfdp; k0 += kFdBatch * nthr) {
                 R eh[kFdBatch];
                 float el[kFdBatch];
 #pragma unroll
                 for (int u = 0; u < kFdBatch; ++u) {
-                    const int i = min(i0 + u * GS, nqp - 1);
+                    const int k = min(k0 + u * nthr, nfdp - 1);
+                    const int i = k - (k >= 2 * nqp ? 2 * nqp : (k >= nqp ? nqp : 0));
                     if constexpr (kMixed) {
                         eh[u] = __ldg(g.proj_e_f + i);
                         el[u] = __ldg(g.proj_e_fl + i);
@@ -559,12 +564,15 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                 }
 #pragma unroll
                 for (int u = 0; u < kFdBatch; ++u) {
-                    const int i = i0 + u * GS;
+                    const int k = k0 + u * nthr;
+                    const int sf = k >= 2 * nqp ? 2 : (k >= nqp ? 1 : 0);
+                    const int i = k - sf * nqp;
                     R fv, fcv = 0;
                     if constexpr (kMixed) {
                         // f and 1 - f from one exp, each without cancellation.  x = (E - mu)/T reaches
                         // ~100 in the tail, where rounding x to FP32 would move exp(-|x|) by ~1e-5 in
                         // steps; x is formed as a double-float, e^-|x| = expf(-|x_hi|) (1 - |x|_lo)
+                        const float muh = os->mu_h[sf], mul = os->mu_l[sf];
                         float e1, e2;
                         const float d0 = two_sum(eh[u], -muh, &e1);
                         const float dh = two_sum(d0, __fadd_rn(e1, __fsub_rn(el[u], mul)), &e2);
@@ -579,12 +587,13 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                         fv = pos ? t * inv : inv;
                         fcv = pos ? inv : t * inv;
                     } else {
+                        const R mu = (R)os->mu[sf];
                         fv = (R)1 / (r_exp((eh[u] - mu) * Tinv) + (R)1);
                     }
-                    if (i < nqp && NMC_IN_BOUNDS(g.dbg, (long long)((kMixed ? NS : 0) + s) * nqp + i,
-                                                 (long long)(kMixed ? 2 : 1) * NS * nqp, kDbgSmemFd)) {
-                        fq[s * nqp + i] = fv;
-                        if constexpr (kMixed) fq[(NS + s) * nqp + i] = fcv;
+                    if (k < nfdp && NMC_IN_BOUNDS(g.dbg, (long long)((kMixed ? NS : 0) + sf) * nqp + i,
+                                                  (long long)(kMixed ? 2 : 1) * NS * nqp, kDbgSmemFd)) {
+                        fq[sf * nqp + i] = fv;
+                        if constexpr (kMixed) fq[(NS + sf) * nqp + i] = fcv;
                     }
                 }
             }
@@ -601,8 +610,9 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                                (long long)g.n_elem * nq * kProjQuad, kDbgProj) ||
                 !NMC_IN_BOUNDS(g.dbg, (long long)s * NEP + e * nq + nq - 1, (long long)NS * NEP, kDbgSmemVec))
                 continue;
-            const R* f = fq + s * nqp + e * kProjQuad;
-            const R* fc = fq + (NS + s) * nqp + e * kProjQuad;
+            const int sfd = s < 2 ? s : 2;   // the heavy flavours' Fermi--Dirac values are species 2's
+            const R* f = fq + sfd * nqp + e * kProjQuad;
+            const R* fc = fq + (NS + sfd) * nqp + e * kProjQuad;
             R avg = 0, avgc = 0, coef[kMaxNq] = {0, 0, 0}, coefc[kMaxNq] = {0, 0, 0};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
