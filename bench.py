@@ -74,8 +74,8 @@ WORKLOAD = ("perturbed collapse profile (+-10% seeded perturbations of rho, T, Y
 # DRAM bytes (read + write) per node of one launch, from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum); traffic grows with the node count.  None where the kernel has changed since its
 # counters were taken.
-TRAFFIC_PER_NODE = {"fused_kernel<double>": 255172096 / 16384, "fused_kernel<float>": 239348736 / 16384,
-                    "adjoint_kernel": 200302336 / 16384, "velocity_kernel": 101233152 / 16384,
+TRAFFIC_PER_NODE = {"fused_kernel<double>": 15540.0, "fused_kernel<float>": 14506.0,
+                    "adjoint_kernel": 12079.0, "velocity_kernel": 6029.0,
                     "c2p_kernel": 530723584 / 65536, "opacity_interp_kernel": 159e6 / (1 << 22),
                     "opacity_interp_mixed_kernel": 162e6 / (1 << 22)}
 
