@@ -30,13 +30,13 @@
 // threads), eps^2-weighted projection and bound limiter per (species, element)
 // (Eq. fermiDiracProjection); trilinear log-table interpolation of chi_EmAb and
 // sigma_Iso with coalesced rows of ne energies; bilinear (log10 T, eta)
-// interpolation of the kernel tables into shared memory, then the NES
-// up-scattering triangle by detailed balance (Eqs. inOutInvarianceNES,
-// detailedBalanceNES).
+// interpolation of the kernel tables into shared memory, each tabulated NES
+// entry written together with its up-scattering mirror by detailed balance
+// (Eqs. inOutInvarianceNES, detailedBalanceNES).
 //
 // Per inner iteration: rates as shared-memory mat-vecs (Phi_In = Phi_Out^T;
 // the antiparticle's Phi_Ann is the transpose; Phi_Pro = a_s(q) a_sbar(q')
-// Phi_Ann with a = D/(1-D) by Eq. detailedBalancePair), the map Q
+// Phi_Ann with a = D^Eq/(1 - D^Eq) by Eq. detailedBalancePair), the map Q
 // (Eq. implicitMomentsNodal, v = 0), one block reduction for the Anderson
 // least-squares entries, the least-squares solve by the lead warp (FP64,
 // lane-parallel), the mixing update, and the Algorithm 2 vote; three barriers.
