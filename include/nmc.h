@@ -141,7 +141,7 @@ typedef struct {
     int32_t m_outer;       /* Anderson memory M_outer, 1 .. 5 */
     int32_t max_inner;     /* cap per inner loop, >= 1 */
     int32_t max_outer;     /* cap on outer iterations, >= 1 */
-    int32_t precision;     /* NMC_FP64 or NMC_MIXED */
+    int32_t precision;     /* NMC_FP64 or NMC_MIXED (mixed: n_q <= 2, else NMC_EUNSUPPORTED) */
     int32_t mode;          /* NMC_MODE_FUSED or NMC_MODE_PLAIN */
     int32_t proc_mask;     /* NMC_PROC_* bits */
     int32_t frozen_matter; /* 1: y fixed at y*, single outer iteration */

@@ -17,7 +17,13 @@ Readings of points the paper leaves open:
   (NQUAD = 16); the mass matrix integrand is a polynomial of degree 2k+2, so
   it is integrated exactly;
 * when the cell average itself lies outside [D_min, D_max] no limiter can keep
-  it, and the element is set to the clamped cell average (constant).
+  it, and the element is set to the clamped cell average (constant);
+* the limited nodal values are clipped to [D_min, D_max]: in exact arithmetic
+  the limiter puts the extreme check point on the bound, but the rounding of
+  avg + theta (D~ - avg) is of the order of the cell average's last digit and
+  can leave that point just outside, below zero where the cell average is far
+  above D_min (quadratic elements on a steep Fermi--Dirac tail); the clip
+  restores the property the limiter states (NaN passes through).
 """
 
 import numpy as np
@@ -70,7 +76,7 @@ def limit_element(coef, avg, nq, dmin, dmax):
         theta = min(theta, (avg - dmin) / (avg - vmin))
     if vmax > dmax:
         theta = min(theta, (dmax - avg) / (vmax - avg))
-    return avg + theta * (coef - avg)
+    return np.minimum(np.maximum(avg + theta * (coef - avg), dmin), dmax)
 
 
 def equilibrium_distribution(grid, mu, T, dmin, dmax, limit=True):

@@ -672,6 +672,16 @@ __device__ void compute_opacities(const DevGrid& g, const DevTables& tb, const n
                     coef[pp] = avg + theta * (coef[pp] - avg);
                     coefc[pp] = avgc + theta * (coefc[pp] - avgc);
                 }
+                // the limiter puts the extreme point on the bound in exact arithmetic; the rounding of
+                // avg + theta (v - avg) can leave it just outside (below zero where avg is far above
+                // d_min, e.g. quadratic elements on a steep tail), so the nodal values are clipped
+                // (comparisons keep a NaN)
+                const R cmin = (R)(1.0 - P.d_max), cmax = (R)(1.0 - P.d_min);
+#pragma unroll
+                for (int pp = 0; pp < kMaxNq; ++pp) {
+                    coef[pp] = coef[pp] < dmin ? dmin : (coef[pp] > dmax ? dmax : coef[pp]);
+                    coefc[pp] = coefc[pp] < cmin ? cmin : (coefc[pp] > cmax ? cmax : coefc[pp]);
+                }
             }
 #pragma unroll
             for (int pp = 0; pp < kMaxNq; ++pp) {

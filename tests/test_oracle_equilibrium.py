@@ -95,6 +95,26 @@ def test_limiter_keeps_bounds_and_k2_undershoot():
         assert np.all(v >= DMIN - slack) and np.all(v <= DMAX + slack), e
 
 
+@pytest.mark.parametrize("nq", [2, 3])
+def test_limited_nodal_values_strictly_inside_bounds(nq):
+    """At the LG nodes the limited values lie in [D_min, D_max] exactly (no rounding slack), so that
+    a = D^Eq / (1 - D^Eq) is finite and positive, over states with steep Fermi--Dirac tails on the
+    coarse and fine grids; without the final clip, the quadratic case rounds some limited nodes to zero
+    or below."""
+    worst = 1.0
+    for n_elem, de1 in ((16, 1.875), (32, 1.0)):
+        edges, _ = ogrid.geometric_edges(n_elem, de1)
+        g = ogrid.EnergyGrid(edges, nq)
+        for T in (0.5, 1.3, 2.7, 8.0, 18.0, 33.0):
+            for mu in (-20.0, 0.0, 5.0, 40.0, 110.0):
+                d = eq.equilibrium_distribution(g, mu, T, DMIN, DMAX)
+                assert np.all(d >= DMIN) and np.all(d <= DMAX), (n_elem, nq, T, mu, d.min(), d.max())
+                a = d / (1.0 - d)
+                assert np.all(np.isfinite(a)) and np.all(a > 0.0)
+                worst = min(worst, float(np.min(d)))
+    assert worst >= DMIN
+
+
 def test_limiter_upper_bound_degenerate():
     """Degenerate state (T = 15, mu = 113): values capped at D_max, averages kept."""
     T, mu = 15.0, 113.0
